@@ -1,0 +1,382 @@
+"""Benchmark of the time-fused stencil sweep on GB300.
+
+One step = one stencil_run of the whole workload: T Jacobi steps over one
+synthetic grid (default: 2D 5-point star, 8192 x 8192 FP32, Dirichlet 0,
+T = 64, inputs uniform[0,1) from a fixed seed), with the fusion depth k the
+plan's autotuner picks.  Reported beside it on the same GB300: the plain
+one-step-per-launch sweep, the HBM roofline fraction of the fused kernel,
+the error against a closed form, an end-to-end number through the host-buffer
+C-ABI call, and the FP64 oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload 2d5p|2d9p|...] [--k K]
+Under torchrun each rank advances its own replica of the grid (weak scaling:
+the single-grid sweep is not domain-decomposed across GPUs).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GStencil/s and % HBM roofline, time-fused vs plain 1-step sweep at stated error"
+
+WORKLOADS = {
+    "2d5p": (synth.c2_2d5p, "f32"),
+    "2d9p": (synth.c2_2d9p, "f32"),
+    "2d5p_f64": (synth.c2_2d5p, "f64"),
+    "2d9p_f64": (synth.c2_2d9p, "f64"),
+    "3d7p": (synth.c3_3d7p, "f32"),
+    "3d27p": (synth.c3_3d27p, "f32"),
+    "3d7p_bf16": (synth.c3_3d7p, "bf16"),
+    "3d27p_bf16": (synth.c3_3d27p, "bf16"),
+    "1d3p_f64": (synth.c1_1d3p, "f64"),
+}
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture, keyed by workload, k and a hash of the kernel sources it was
+# measured on; reported as null once those sources change.
+NCU_TRAFFIC = {}
+
+KERNEL_SOURCES = ["paper_2103_08825_gb300/csrc/k_fused2d.cuh", "paper_2103_08825_gb300/csrc/common.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd[1:1] = ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(p, budget_s: float):
+    """Time the FP64 oracle (as it stands) on a bounded sample of workload p:
+    the first rows of the grid for a few steps, sized to about budget_s."""
+    import oracle
+    oracle.build()
+    d = p.d
+    rows = p.shape[0]
+    sub = list(p.shape)
+    steps = 1
+    # start small, grow until the run takes a measurable fraction of the budget
+    sub[0] = max(1, min(rows, 64))
+    while True:
+        u0 = synth.uniform01(p.seed, int(np.prod(sub))).reshape(sub)
+        t0 = time.perf_counter()
+        oracle.run(d, p.r, p.pattern, tuple(sub), p.weights, p.bkind, p.bval, u0, steps)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or (sub[0] == rows and steps >= p.T):
+            break
+        grow = max(2.0, min(16.0, (budget_s / 2) / max(dt, 1e-4)))
+        if sub[0] < rows:
+            sub[0] = min(rows, int(sub[0] * grow))
+        else:
+            steps = min(p.T, int(steps * grow) + 1)
+    upd = float(np.prod(sub)) * steps
+    desc = f"oracle FP64 on the first {sub[0]} of {rows} outer rows of the same grid, {steps} of {p.T} steps"
+    return upd / dt / 1e9, desc, dt
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample of the workload."""
+    maker, _ = WORKLOADS[args.workload]
+    p = maker()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    total = args.steps + args.warmup
+    per_step_budget = max(0.05, min(2.0, 150.0 / max(1, total)))
+    rate, desc, _ = oracle_sample(p, per_step_budget)
+    # fixed sample for all steps
+    sub = list(p.shape)
+    upd_target = rate * 1e9 * per_step_budget
+    inner = float(np.prod(p.shape[1:])) if p.d > 1 else 1.0
+    steps = 1
+    if p.d > 1:
+        sub[0] = int(max(1, min(p.shape[0], upd_target / inner)))
+    else:
+        sub[0] = int(max(64, min(p.shape[0], upd_target)))
+    u0 = synth.uniform01(p.seed, int(np.prod(sub))).reshape(sub)
+    for _ in range(args.warmup):
+        oracle.run(p.d, p.r, p.pattern, tuple(sub), p.weights, p.bkind, p.bval, u0, steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(p.d, p.r, p.pattern, tuple(sub), p.weights, p.bkind, p.bval, u0, steps)
+    dt = time.perf_counter() - t0
+    upd = float(np.prod(sub)) * steps * args.steps
+    value = upd / dt / 1e9
+    sample = f"FP64 oracle on the first {sub[0]} of {p.shape[0]} outer rows, {steps} step per bench step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GStencil/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform[0,1))",
+            "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T},
+            "cpu_baseline": {"value": value, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GStencil/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(key, p):
+    dt = WORKLOADS[key][1].upper()
+    shape = "x".join(str(s) for s in p.shape)
+    bnd = "Dirichlet-0" if p.bkind == synth.DIRICHLET else "periodic"
+    return f"{p.name} {shape} {dt} T={p.T} {bnd}"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d5p", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=0, help="fusion depth (0 = autotune)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=0, help="steps for the plain sweep (0 = steps/4)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2103_08825_gb300 as sg
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sg.load()
+
+    maker, dtn = WORKLOADS[args.workload]
+    p = maker()
+    code = {"f32": sg.STENCIL_F32, "f64": sg.STENCIL_F64, "bf16": sg.STENCIL_BF16}[dtn]
+    tdt = sg.torch_dtype(code)
+    esize = torch.tensor([], dtype=tdt).element_size()
+    plan = sg.stencil_plan_create(p.d, p.r, p.shape, p.pattern, p.weights, p.bkind, p.bval, code)
+    stream = torch.cuda.current_stream()
+
+    u0 = torch.from_numpy(synth.uniform01(p.seed, p.npts).reshape(p.shape)).to(tdt)
+    x = u0.to(dev)
+    y = torch.empty_like(x)
+
+    if args.k > 0:
+        sg.stencil_plan_set_k(plan, args.k)
+        tuned = None
+    else:
+        tuned = sg.stencil_plan_tune(plan, p.T)
+    k = sg.stencil_plan_get_k(plan)
+    launches = sg.stencil_plan_launch_count(plan, p.T)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def fused_step():
+        sg.stencil_run(plan, x, y, p.T, stream)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid if rank == 0 else None)
+    if rank == 0:
+        clocks.start()
+    ms_total = timed(fused_step, args.steps, args.warmup)
+    clk = clocks.stop() if rank == 0 else None
+    if sg.stencil_get_device_status(plan) != 0:
+        raise RuntimeError("device status word reports a timeout")
+    ms_step = ms_total / args.steps
+    upd_step = float(p.npts) * p.T
+    value = upd_step * world / (ms_step * 1e-3) / 1e9
+
+    # plain one-step-per-launch sweep on the same grid and GPU
+    sg.stencil_plan_set_variant(plan, sg.STENCIL_VARIANT_PLAIN)
+    plain_steps = args.plain_steps or max(3, args.steps // 4)
+    ms_plain = timed(fused_step, plain_steps, 3) / plain_steps
+    sg.stencil_plan_set_variant(plan, sg.STENCIL_VARIANT_FUSED)
+    plain_value = upd_step / (ms_plain * 1e-3) / 1e9
+
+    # roofline of the dominant (fused) kernel: algorithmic bytes per launch
+    # (one read and one write of every point) / average launch duration
+    peak, peak_kind = measured_peaks()
+    bytes_launch = 2.0 * p.npts * esize
+    avg_launch_s = ms_step * 1e-3 / launches
+    achieved = bytes_launch / avg_launch_s / 1e9
+    key = f"{args.workload}:k{k}:{kernel_hash()}"
+    traffic = NCU_TRAFFIC.get(key)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": sg.stencil_plan_describe(plan),
+                "bytes_per_launch": bytes_launch, "launches_per_step": launches}
+
+    # error at the timed configuration: a Dirichlet sine mode must decay by
+    # lam^T (closed form, no oracle involved)
+    err = None
+    if p.d == 2 and p.bkind == synth.DIRICHLET and p.r == 1:
+        ny, nx = p.shape
+        ky, kx = 3, 5
+        phi = np.multiply.outer(synth.sine_mode_1d(ny, ky), synth.sine_mode_1d(nx, kx))
+        w = synth.f32_weights(p.weights) if dtn != "f64" else p.weights
+        offs = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)] if p.pattern == synth.STAR else \
+            [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
+        lam = sum(w[j] * np.cos(np.pi * ky * o[0] / (ny + 1)) * np.cos(np.pi * kx * o[1] / (nx + 1))
+                  for j, o in enumerate(offs))
+        xm = torch.from_numpy(phi).to(tdt).to(dev)
+        ym = torch.empty_like(xm)
+        sg.stencil_run(plan, xm, ym, p.T, stream)
+        torch.cuda.synchronize()
+        got = ym.double().cpu().numpy()
+        err = {"kind": "Dirichlet sine mode (ky=3, kx=5) against lam^T * mode, full grid",
+               "max_abs": float(np.max(np.abs(got - lam ** p.T * phi))), "tolerance": 1e-5 if dtn == "f32" else 1e-12}
+        del xm, ym
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    h_in = u0.pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+
+    def e2e_step():
+        sg.stencil_run_host(plan, h_in, h_out, p.T, stream)
+
+    e2e_steps = max(3, args.steps // 10)
+    ms_e2e = timed(e2e_step, e2e_steps, 2) / e2e_steps
+    e2e = {"value": upd_step * world / (ms_e2e * 1e-3) / 1e9, "unit": "GStencil/s",
+           "h2d_bytes_per_step": p.npts * esize, "d2h_bytes_per_step": p.npts * esize,
+           "ms_per_step": ms_e2e, "call": "stencil_run_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rate, desc, secs = oracle_sample(p, 20.0)
+        cpu = {"value": rate, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": desc + f" ({secs:.1f} s)", "host_cores": host_cores()}
+
+    line = {"metric": METRIC, "value": value, "unit": "GStencil/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtn, "data": "synthetic (seeded uniform[0,1), fixed boundary)",
+            "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T, "k": k,
+                       "tuned": {"k": tuned[0], "ms": tuned[1]} if tuned else None,
+                       "l2": f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "plain_sweep": {"value": plain_value, "unit": "GStencil/s", "ms_per_step": ms_plain,
+                            "launches_per_step": p.T},
+            "speedup_vs_plain": value / world / plain_value,
+            "error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * stencil.h -- C ABI of the GB300 (sm_103a) iterated-stencil library.
+ *
+ * The library advances d-dimensional grids (d = 1, 2, 3) by T Jacobi time
+ * steps of a star or box stencil of order r.  The operation is the one the
+ * paper defines in Section 1: every grid point at time t+1 is a weighted sum
+ * of its (2r+1)-per-dimension neighbours at time t, the time loop outermost.
+ * Several time steps are fused into each pass over HBM, the GPU counterpart
+ * of the paper's time-loop unroll-and-jam (Section 3.3, Algorithm 1).
+ *
+ * Conventions (the paper leaves them open; the library fixes them):
+ *   grid     interior points only, dense, row-major, outermost dimension
+ *            first, innermost (unit-stride, "x") dimension last;
+ *   update   u_{t+1}[x] = sum_{o in S} w_o * u_t(x + o)   (a correlation);
+ *   S        box: [-r, r]^d;  star: {0} and {+-j e_a : 1 <= j <= r};
+ *   weights  compact order.  box: (2r+1)^d values, offsets lexicographic
+ *            (o_0, ..., o_{d-1}) with the innermost dimension fastest;
+ *            star: 1 + 2dr values [centre, axis 0: -r..-1, +1..+r, axis 1:
+ *            ..., ...], axis 0 being the outermost dimension;
+ *   boundary DIRICHLET: out-of-domain values are the constant `value` at
+ *            every time level; PERIODIC: indices wrap modulo the extent;
+ *   order    each sum is evaluated as one multiply followed by fused
+ *            multiply-adds over the offsets in lexicographic order, so every
+ *            fusion depth k gives bit-identical results;
+ *   dtypes   F64 (FP64 math), F32 (FP32 math), BF16 and F16 (storage only:
+ *            FP32 math, one round-to-nearest-even per fused pass), I32
+ *            (uint32 wraparound arithmetic, bit-exact; weights and the
+ *            boundary value must be integers).
+ *
+ * Ownership and errors (all entry points):
+ *   - Device pointers are plain CUDA device addresses (for example a torch
+ *     tensor's data_ptr()), owned by the caller, contiguous, of the plan's
+ *     dtype and shape.  `stream` is a cudaStream_t (NULL = legacy default).
+ *   - All device work is enqueued asynchronously on `stream`; host pointers
+ *     are only read during the call unless stated otherwise.
+ *   - Argument, shape and support errors are returned before anything is
+ *     enqueued.  CUDA errors return STENCIL_ERR_CUDA.  A device-side bounded
+ *     wait that gives up records STENCIL_ERR_TIMEOUT in the plan's device
+ *     status word, read by stencil_get_device_status.
+ *   - No C++ exception crosses this interface.  A plan may be used by one
+ *     host thread at a time; calls on different streams with the same plan
+ *     share its workspace and must not overlap.
+ *   - stencil_last_error() returns a message for the calling thread's most
+ *     recent failing call.
+ */
+#ifndef STENCIL_GB300_H
+#define STENCIL_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_plan_s *stencil_plan_t;
+typedef struct stencil_batch_s *stencil_batch_t;
+
+typedef enum {
+    STENCIL_OK = 0,
+    STENCIL_ERR_INVALID_ARG = 1,
+    STENCIL_ERR_UNSUPPORTED = 2,
+    STENCIL_ERR_OOM = 3,
+    STENCIL_ERR_CUDA = 4,
+    STENCIL_ERR_TIMEOUT = 5,
+    STENCIL_ERR_INTERNAL = 6
+} stencil_status_t;
+
+typedef enum { STENCIL_F64 = 0, STENCIL_F32 = 1, STENCIL_BF16 = 2, STENCIL_F16 = 3, STENCIL_I32 = 4 } stencil_dtype_t;
+typedef enum { STENCIL_STAR = 0, STENCIL_BOX = 1 } stencil_pattern_t;
+typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_kind_t;
+
+/* Which kernels stencil_run uses.  FUSED: k steps per pass (the default);
+ * PLAIN: one step per launch, each thread reading its own neighbours -- the
+ * one-step-per-launch sweep the fused path is measured against. */
+typedef enum { STENCIL_VARIANT_FUSED = 0, STENCIL_VARIANT_PLAIN = 1 } stencil_variant_t;
+
+/* Stencil coefficients: `count` values in compact order (see above). */
+typedef struct {
+    int32_t pattern; /* stencil_pattern_t */
+    int32_t count;   /* must equal (2r+1)^d (box) or 1+2dr (star) */
+    const double *w; /* host pointer, read during the call */
+} stencil_weights_t;
+
+typedef struct {
+    int32_t kind;    /* stencil_boundary_kind_t */
+    double value;    /* Dirichlet value (ignored when periodic) */
+} stencil_boundary_t;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Create a plan for one grid geometry (Section 1: dimension d, order r,
+ * weighted sum over the neighbourhood).  `shape` holds d extents, outermost
+ * first, each >= 1.  1 <= dim <= 3, 1 <= radius <= 3.  Allocates nothing on
+ * the device until first use.  On success *out owns the plan. */
+stencil_status_t stencil_plan_create(stencil_plan_t *out, int32_t dim, int32_t radius, const int64_t *shape,
+                                     const stencil_weights_t *weights, const stencil_boundary_t *boundary,
+                                     int32_t dtype);
+
+/* Release a plan and its device workspace (synchronises its device). */
+stencil_status_t stencil_plan_destroy(stencil_plan_t plan);
+
+/* Fusion depth k (time steps per pass, the paper's unrolling factor of
+ * Section 3.3).  0 selects the plan's default; values above the kernels'
+ * limit for this geometry return STENCIL_ERR_UNSUPPORTED. */
+stencil_status_t stencil_plan_set_k(stencil_plan_t plan, int32_t k);
+stencil_status_t stencil_plan_get_k(stencil_plan_t plan, int32_t *k);
+/* Largest k the fused kernels accept for this plan. */
+stencil_status_t stencil_plan_max_k(stencil_plan_t plan, int32_t *kmax);
+
+/* Select FUSED (default) or PLAIN kernels for stencil_run. */
+stencil_status_t stencil_plan_set_variant(stencil_plan_t plan, int32_t variant);
+
+/* Autotune the fusion depth: times stencil_run for every supported k on
+ * plan-owned buffers holding zeros, with CUDA events on `stream`, and keeps
+ * the fastest.  Synchronises `stream`.  `T` is the step count to tune for;
+ * best_k / best_ms (may be NULL) receive the choice and its time. */
+stencil_status_t stencil_plan_tune(stencil_plan_t plan, int64_t T, void *stream, int32_t *best_k, double *best_ms);
+
+/* Number of kernel launches stencil_run makes for T steps with the current
+ * variant and k (ceil(T/k) fused passes, or T plain steps). */
+stencil_status_t stencil_plan_launch_count(stencil_plan_t plan, int64_t T, int64_t *launches);
+
+/* Short text naming the kernel, k and tiling the plan uses (for logs). */
+stencil_status_t stencil_plan_describe(stencil_plan_t plan, char *buf, int32_t len);
+
+/* ------------------------------------------------------------------ sweep */
+
+/* u_out := T Jacobi steps applied to u_in (Section 1; fused per Section 3.3).
+ * Both are device pointers of the plan's shape and dtype; u_in is only read;
+ * u_out must not overlap u_in.  T = 0 copies.  Intermediate passes use a
+ * plan-owned device buffer of one grid, allocated on first use. */
+stencil_status_t stencil_run(stencil_plan_t plan, const void *u_in, void *u_out, int64_t T, void *stream);
+
+/* Same computation on HOST buffers: copies h_in to the device, runs T steps,
+ * copies the result to h_out, and synchronises `stream` before returning.
+ * Uses two plan-owned device grids.  Pinned host memory makes the copies
+ * asynchronous engine transfers; pageable memory works but is slower. */
+stencil_status_t stencil_run_host(stencil_plan_t plan, const void *h_in, void *h_out, int64_t T, void *stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/* A batch of `n` independent 2D grids of one dtype, order and boundary, each
+ * with its own shape (shapes: n x dim, outermost first), coefficients
+ * (weights[i]) and step count (T[i] >= 0).  All grids are advanced together
+ * by one persistent kernel that takes (pass, grid, tile) work items from a
+ * queue, waiting with bounded spins for the neighbouring tiles of the
+ * previous pass; the first stencil_batch_run captures that launch into a
+ * CUDA graph which later calls replay.  The batch owns one workspace grid per
+ * member.  Only dim = 2 and dtype F32 / I32 are supported. */
+stencil_status_t stencil_batch_create(stencil_batch_t *out, int32_t n, int32_t dim, int32_t radius,
+                                      const int64_t *shapes, const stencil_weights_t *weights, const int64_t *T,
+                                      const stencil_boundary_t *boundary, int32_t dtype);
+stencil_status_t stencil_batch_destroy(stencil_batch_t batch);
+
+/* u_out[i] := T[i] steps applied to u_in[i] for every member.  u_in, u_out:
+ * host arrays of n device pointers (read during the call).  Every u_out[i]
+ * must differ from every u_in[j].  Bounded waits that give up record
+ * STENCIL_ERR_TIMEOUT, read by stencil_batch_get_device_status. */
+stencil_status_t stencil_batch_run(stencil_batch_t batch, const void *const *u_in, void *const *u_out,
+                                   void *stream);
+stencil_status_t stencil_batch_get_device_status(stencil_batch_t batch);
+/* Kernel launches per stencil_batch_run (the graph's kernel nodes). */
+stencil_status_t stencil_batch_launch_count(stencil_batch_t batch, int64_t *launches);
+
+/* ----------------------------------------------------------------- adjoint */
+
+/* Reverse-mode derivative of u_T = (T steps)(u0) for F32 plans: given
+ * grad_uT = dL/du_T (device, plan shape), writes grad_u0 = dL/du0 (device,
+ * plan shape) and grad_w[j] = dL/dw_j (device, `count` doubles, compact
+ * order).  The transposed sweep runs backward in time; forward states are
+ * recomputed from checkpoints stored every `ckpt_every` steps (1 <= ckpt_every
+ * <= T; the plan keeps ceil(T/ckpt_every) + ckpt_every grids of workspace).
+ * With a Dirichlet boundary the weight gradient includes the boundary value's
+ * contributions. */
+stencil_status_t stencil_adjoint_run(stencil_plan_t plan, const void *u0, const void *grad_uT, int64_t T,
+                                     int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream);
+
+/* -------------------------------------------------------------- reductions */
+
+typedef enum {
+    STENCIL_REDUCE_SUM = 0,       /* sum u                       */
+    STENCIL_REDUCE_SUMSQ = 1,     /* sum u^2                     */
+    STENCIL_REDUCE_HALF_SQDIST = 2 /* 0.5 * sum (u - target)^2  */
+} stencil_reduce_op_t;
+
+/* FP64 reduction over n elements of dtype `dtype` (F64, F32, BF16, F16):
+ * elements are widened to FP64 and summed in a fixed order (deterministic).
+ * `target` is used only by HALF_SQDIST.  The result is written to the device
+ * double *out.  Per-block partial sums live in a library-owned device buffer
+ * of the current device, allocated on first use and grown as needed. */
+stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void *u, const void *target, int32_t op,
+                                double *out, void *stream);
+
+/* ------------------------------------------------------------------ status */
+
+/* Synchronises the plan's device and returns (then clears) its device
+ * status word: STENCIL_OK or STENCIL_ERR_TIMEOUT. */
+stencil_status_t stencil_get_device_status(stencil_plan_t plan);
+const char *stencil_status_string(stencil_status_t status);
+const char *stencil_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_GB300_H */

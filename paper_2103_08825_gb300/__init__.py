@@ -1,0 +1,248 @@
+"""Python binding of the GB300 iterated-stencil library (``include/stencil.h``).
+
+Argument marshalling only: every step of the sweep runs in the CUDA kernels of
+``libstencil_gb300.so``.  Functions carry the C names; tensors are passed as
+device pointers (``data_ptr()``) and streams as ``cudaStream_t`` handles.
+There is no CPU fallback: if the library is missing, ``load()`` raises.
+
+The method (paper, Sections 1 and 3.3): T Jacobi steps of a star or box
+stencil of order r, k steps fused per pass over memory.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libstencil_gb300.so")
+
+STENCIL_OK, STENCIL_ERR_INVALID_ARG, STENCIL_ERR_UNSUPPORTED, STENCIL_ERR_OOM = 0, 1, 2, 3
+STENCIL_ERR_CUDA, STENCIL_ERR_TIMEOUT, STENCIL_ERR_INTERNAL = 4, 5, 6
+STENCIL_F64, STENCIL_F32, STENCIL_BF16, STENCIL_F16, STENCIL_I32 = 0, 1, 2, 3, 4
+STENCIL_STAR, STENCIL_BOX = 0, 1
+STENCIL_DIRICHLET, STENCIL_PERIODIC = 0, 1
+STENCIL_VARIANT_FUSED, STENCIL_VARIANT_PLAIN = 0, 1
+STENCIL_REDUCE_SUM, STENCIL_REDUCE_SUMSQ, STENCIL_REDUCE_HALF_SQDIST = 0, 1, 2
+
+# Every symbol include/stencil.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "stencil_plan_create", "stencil_plan_destroy", "stencil_plan_set_k", "stencil_plan_get_k",
+    "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_tune", "stencil_plan_launch_count",
+    "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_batch_create",
+    "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status",
+    "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_reduce", "stencil_get_device_status",
+    "stencil_status_string", "stencil_last_error",
+]
+
+
+class StencilError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str):
+        super().__init__(f"{what}: {detail} (status {status})")
+        self.status = status
+
+
+class stencil_weights_t(ctypes.Structure):
+    _fields_ = [("pattern", ctypes.c_int32), ("count", ctypes.c_int32), ("w", ctypes.POINTER(ctypes.c_double))]
+
+
+class stencil_boundary_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libstencil_gb300.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA stencil library not built: {p} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "stencil_plan_create": (st, [ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i64), ctypes.POINTER(stencil_weights_t),
+                                     ctypes.POINTER(stencil_boundary_t), i32]),
+        "stencil_plan_destroy": (st, [vp]),
+        "stencil_plan_set_k": (st, [vp, i32]),
+        "stencil_plan_get_k": (st, [vp, ctypes.POINTER(i32)]),
+        "stencil_plan_max_k": (st, [vp, ctypes.POINTER(i32)]),
+        "stencil_plan_set_variant": (st, [vp, i32]),
+        "stencil_plan_tune": (st, [vp, i64, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+        "stencil_plan_launch_count": (st, [vp, i64, ctypes.POINTER(i64)]),
+        "stencil_plan_describe": (st, [vp, ctypes.c_char_p, i32]),
+        "stencil_run": (st, [vp, vp, vp, i64, vp]),
+        "stencil_run_host": (st, [vp, vp, vp, i64, vp]),
+        "stencil_batch_create": (st, [ctypes.POINTER(vp), i32, i32, i32, ctypes.POINTER(i64),
+                                      ctypes.POINTER(stencil_weights_t), ctypes.POINTER(i64),
+                                      ctypes.POINTER(stencil_boundary_t), i32]),
+        "stencil_batch_destroy": (st, [vp]),
+        "stencil_batch_run": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
+        "stencil_batch_get_device_status": (st, [vp]),
+        "stencil_batch_launch_count": (st, [vp, ctypes.POINTER(i64)]),
+        "stencil_adjoint_run": (st, [vp, vp, vp, i64, i32, vp, vp, vp]),
+        "stencil_reduce": (st, [i32, i64, vp, vp, i32, vp, vp]),
+        "stencil_get_device_status": (st, [vp]),
+        "stencil_status_string": (ctypes.c_char_p, [st]),
+        "stencil_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != STENCIL_OK:
+        lib = load()
+        raise StencilError(status, what, lib.stencil_last_error().decode(errors="replace"))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.float64: STENCIL_F64, torch.float32: STENCIL_F32, torch.bfloat16: STENCIL_BF16,
+         torch.float16: STENCIL_F16, torch.int32: STENCIL_I32}
+    if t not in m:
+        raise TypeError(f"unsupported dtype {t}")
+    return m[t]
+
+
+def torch_dtype(code: int):
+    import torch
+    return {STENCIL_F64: torch.float64, STENCIL_F32: torch.float32, STENCIL_BF16: torch.bfloat16,
+            STENCIL_F16: torch.float16, STENCIL_I32: torch.int32}[code]
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns a stencil_plan_t (destroyed with the object)."""
+
+    def __init__(self, handle, dim, radius, shape, pattern, weights, bkind, bval, dtype):
+        self.handle = handle
+        self.dim, self.radius, self.shape = dim, radius, tuple(int(s) for s in shape)
+        self.pattern, self.weights, self.bkind, self.bval, self.dtype = pattern, list(weights), bkind, bval, dtype
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.stencil_plan_destroy(h)
+            self.handle = None
+
+    @property
+    def torch_dtype(self):
+        return torch_dtype(self.dtype)
+
+
+def stencil_plan_create(dim: int, radius: int, shape, pattern: int, weights, bkind: int = STENCIL_DIRICHLET,
+                        bval: float = 0.0, dtype: int = STENCIL_F32) -> Plan:
+    lib = load()
+    n = (ctypes.c_int64 * dim)(*[int(s) for s in shape])
+    warr = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
+    w = stencil_weights_t(pattern, len(weights), warr)
+    b = stencil_boundary_t(bkind, float(bval))
+    h = ctypes.c_void_p()
+    _check(lib.stencil_plan_create(ctypes.byref(h), dim, radius, n, ctypes.byref(w), ctypes.byref(b), dtype),
+           "stencil_plan_create")
+    return Plan(h, dim, radius, shape, pattern, weights, bkind, bval, dtype)
+
+
+def stencil_plan_set_k(plan: Plan, k: int):
+    _check(load().stencil_plan_set_k(plan.handle, int(k)), "stencil_plan_set_k")
+
+
+def stencil_plan_get_k(plan: Plan) -> int:
+    k = ctypes.c_int32()
+    _check(load().stencil_plan_get_k(plan.handle, ctypes.byref(k)), "stencil_plan_get_k")
+    return k.value
+
+
+def stencil_plan_max_k(plan: Plan) -> int:
+    k = ctypes.c_int32()
+    _check(load().stencil_plan_max_k(plan.handle, ctypes.byref(k)), "stencil_plan_max_k")
+    return k.value
+
+
+def stencil_plan_set_variant(plan: Plan, variant: int):
+    _check(load().stencil_plan_set_variant(plan.handle, int(variant)), "stencil_plan_set_variant")
+
+
+def stencil_plan_tune(plan: Plan, T: int, stream=None):
+    k = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(load().stencil_plan_tune(plan.handle, int(T), _stream_handle(stream), ctypes.byref(k), ctypes.byref(ms)),
+           "stencil_plan_tune")
+    return k.value, ms.value
+
+
+def stencil_plan_launch_count(plan: Plan, T: int) -> int:
+    n = ctypes.c_int64()
+    _check(load().stencil_plan_launch_count(plan.handle, int(T), ctypes.byref(n)), "stencil_plan_launch_count")
+    return n.value
+
+
+def stencil_plan_describe(plan: Plan) -> str:
+    buf = ctypes.create_string_buffer(256)
+    _check(load().stencil_plan_describe(plan.handle, buf, 256), "stencil_plan_describe")
+    return buf.value.decode()
+
+
+def _check_grid(plan: Plan, t, name: str):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if tuple(t.shape) != plan.shape or _dtype_code(t.dtype) != plan.dtype:
+        raise ValueError(f"{name} must have shape {plan.shape} and the plan's dtype")
+
+
+def stencil_run(plan: Plan, u_in, u_out, T: int, stream=None):
+    """u_out := T steps applied to u_in (both CUDA tensors of the plan's shape)."""
+    _check_grid(plan, u_in, "u_in")
+    _check_grid(plan, u_out, "u_out")
+    _check(load().stencil_run(plan.handle, ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(u_out.data_ptr()),
+                              int(T), _stream_handle(stream)), "stencil_run")
+    return u_out
+
+
+def stencil_run_host(plan: Plan, h_in, h_out, T: int, stream=None):
+    """Host-buffer run (numpy arrays or CPU tensors); synchronises."""
+    def ptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    _check(load().stencil_run_host(plan.handle, ctypes.c_void_p(ptr(h_in)), ctypes.c_void_p(ptr(h_out)), int(T),
+                                   _stream_handle(stream)), "stencil_run_host")
+    return h_out
+
+
+def stencil_get_device_status(plan: Plan) -> int:
+    return int(load().stencil_get_device_status(plan.handle))
+
+
+def stencil_reduce(u, op: int, target=None, out=None, stream=None):
+    """FP64 reduction of a CUDA tensor; returns the 1-element float64 CUDA tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+    tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
+    _check(load().stencil_reduce(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
+                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "stencil_reduce")
+    return out
+
+
+def stencil_status_string(status: int) -> str:
+    return load().stencil_status_string(int(status)).decode()
+
+
+def stencil_last_error() -> str:
+    return load().stencil_last_error().decode()

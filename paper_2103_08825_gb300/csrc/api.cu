@@ -1,0 +1,426 @@
+// api.cu -- C ABI of the stencil library: plan validation and bookkeeping,
+// the pass loop of stencil_run (Section 3.3's "Main": advance k steps per
+// pass until T is reached), host-buffer runs, the fusion-depth autotuner and
+// status reporting.  No C++ exception crosses this boundary.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace sg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+size_t dtype_size(int dtype) {
+    switch (dtype) {
+        case STENCIL_F64: return 8;
+        case STENCIL_F32: return 4;
+        case STENCIL_BF16: return 2;
+        case STENCIL_F16: return 2;
+        case STENCIL_I32: return 4;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------ TMA maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_tmap(CUtensorMap *map, int dtype, int rank, const int64_t *dims, const uint32_t *box, const void *base) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMapDataType t;
+    switch (dtype) {
+        case STENCIL_F64: t = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+        case STENCIL_F32: t = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+        case STENCIL_BF16: t = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+        case STENCIL_F16: t = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+        case STENCIL_I32: t = CU_TENSOR_MAP_DATA_TYPE_INT32; break;
+        default: return false;
+    }
+    cuuint64_t gdim[3], gstride[2];
+    cuuint32_t bdim[3], estr[3] = {1, 1, 1};
+    uint64_t pitch = dtype_size(dtype);
+    for (int i = 0; i < rank; ++i) {
+        gdim[i] = (cuuint64_t)dims[i];
+        bdim[i] = box[i];
+        if (i > 0) gstride[i - 1] = pitch;
+        pitch *= (uint64_t)dims[i];
+    }
+    CUresult r = fn(map, t, (cuuint32_t)rank, const_cast<void *>(base), gdim, gstride, bdim, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------ helpers
+static int npoints(int d, int r, int pattern) {
+    if (pattern == STENCIL_BOX) {
+        int p = 1;
+        for (int a = 0; a < d; ++a) p *= 2 * r + 1;
+        return p;
+    }
+    return 1 + 2 * d * r;
+}
+
+// Offsets in compact weight order (box lexicographic, innermost fastest;
+// star [centre, axis 0: -r..-1, +1..+r, axis 1: ...]), padded to 3D.
+static void compact_offsets(int d, int r, int pattern, int (*off)[3]) {
+    const int np = npoints(d, r, pattern);
+    for (int j = 0; j < np; ++j) off[j][0] = off[j][1] = off[j][2] = 0;
+    if (pattern == STENCIL_BOX) {
+        for (int j = 0; j < np; ++j) {
+            int rem = j;
+            for (int a = d - 1; a >= 0; --a) {
+                off[j][3 - d + a] = rem % (2 * r + 1) - r;
+                rem /= 2 * r + 1;
+            }
+        }
+    } else {
+        int j = 1;
+        for (int a = 0; a < d; ++a)
+            for (int m = -r; m <= r; ++m)
+                if (m != 0) off[j++][3 - d + a] = m;
+    }
+}
+
+static stencil_status_t cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return STENCIL_ERR_CUDA;
+}
+
+static stencil_status_t ensure_status_word(stencil_plan_s *P) {
+    if (P->d_status) return STENCIL_OK;
+    cudaError_t e = cudaMalloc(&P->d_status, sizeof(int));
+    if (e != cudaSuccess) { P->d_status = nullptr; set_error("status word allocation failed"); return STENCIL_ERR_OOM; }
+    e = cudaMemset(P->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    return STENCIL_OK;
+}
+
+static stencil_status_t ensure_buf(void **buf, size_t bytes) {
+    if (*buf) return STENCIL_OK;
+    cudaError_t e = cudaMalloc(buf, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        cudaGetLastError();
+        set_error("workspace allocation of " + std::to_string(bytes) + " bytes failed");
+        return STENCIL_ERR_OOM;
+    }
+    return STENCIL_OK;
+}
+
+static int effective_k(const stencil_plan_s *P) {
+    const int km = fused_max_k(*P);
+    if (km <= 0) return 1;
+    int k = P->k > 0 ? P->k : std::min(km, P->dtype == STENCIL_F64 ? 1 : 4);
+    return std::min(k, km);
+}
+
+static bool uses_fused(const stencil_plan_s *P) {
+    return P->variant == STENCIL_VARIANT_FUSED && fused_max_k(*P) > 0;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" {
+
+const char *stencil_status_string(stencil_status_t s) {
+    switch (s) {
+        case STENCIL_OK: return "ok";
+        case STENCIL_ERR_INVALID_ARG: return "invalid argument";
+        case STENCIL_ERR_UNSUPPORTED: return "unsupported";
+        case STENCIL_ERR_OOM: return "out of device memory";
+        case STENCIL_ERR_CUDA: return "CUDA error";
+        case STENCIL_ERR_TIMEOUT: return "device-side wait timed out";
+        case STENCIL_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *stencil_last_error(void) { return g_last_error.c_str(); }
+
+stencil_status_t stencil_plan_create(stencil_plan_t *out, int32_t dim, int32_t radius, const int64_t *shape,
+                                     const stencil_weights_t *weights, const stencil_boundary_t *boundary,
+                                     int32_t dtype) {
+    if (!out || !shape || !weights || !boundary) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (dim < 1 || dim > 3) { set_error("dim must be 1, 2 or 3"); return STENCIL_ERR_INVALID_ARG; }
+    if (radius < 1 || radius > 3) { set_error("radius must be 1..3"); return STENCIL_ERR_INVALID_ARG; }
+    if (weights->pattern != STENCIL_STAR && weights->pattern != STENCIL_BOX) {
+        set_error("pattern must be STAR or BOX");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (boundary->kind != STENCIL_DIRICHLET && boundary->kind != STENCIL_PERIODIC) {
+        set_error("boundary kind must be DIRICHLET or PERIODIC");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (dtype < STENCIL_F64 || dtype > STENCIL_I32) { set_error("unknown dtype"); return STENCIL_ERR_INVALID_ARG; }
+    const int np = npoints(dim, radius, weights->pattern);
+    if (weights->count != np || !weights->w) {
+        set_error("weights.count must be " + std::to_string(np));
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    int64_t npts = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (shape[a] < 1 || shape[a] > (int64_t(1) << 40)) { set_error("extents must be >= 1"); return STENCIL_ERR_INVALID_ARG; }
+        if (npts > (int64_t(1) << 62) / shape[a]) { set_error("grid too large"); return STENCIL_ERR_INVALID_ARG; }
+        npts *= shape[a];
+    }
+    for (int j = 0; j < np; ++j) {
+        const double w = weights->w[j];
+        if (!std::isfinite(w)) { set_error("weights must be finite"); return STENCIL_ERR_INVALID_ARG; }
+        if (dtype == STENCIL_I32 && (w != std::floor(w) || std::fabs(w) > 9.0e15)) {
+            set_error("integer mode needs integer weights");
+            return STENCIL_ERR_INVALID_ARG;
+        }
+    }
+    if (dtype == STENCIL_I32 && boundary->kind == STENCIL_DIRICHLET &&
+        (boundary->value != std::floor(boundary->value) || std::fabs(boundary->value) > 9.0e15)) {
+        set_error("integer mode needs an integer boundary value");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    stencil_plan_s *P = new (std::nothrow) stencil_plan_s();
+    if (!P) { set_error("host allocation failed"); return STENCIL_ERR_OOM; }
+    P->dim = dim;
+    P->r = radius;
+    P->pattern = weights->pattern;
+    P->np = np;
+    P->dtype = dtype;
+    P->bkind = boundary->kind;
+    P->bval = boundary->kind == STENCIL_DIRICHLET ? boundary->value : 0.0;
+    for (int a = 0; a < dim; ++a) P->n[3 - dim + a] = shape[a];
+    P->npts = npts;
+    P->grid_bytes = (size_t)npts * dtype_size(dtype);
+    int off[kHostMaxPts][3];
+    compact_offsets(dim, radius, weights->pattern, off);
+    std::vector<int> order(np);
+    for (int j = 0; j < np; ++j) { order[j] = j; P->w_compact[j] = weights->w[j]; }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        for (int c = 0; c < 3; ++c)
+            if (off[a][c] != off[b][c]) return off[a][c] < off[b][c];
+        return false;
+    });
+    for (int j = 0; j < np; ++j) {
+        P->eval_to_compact[j] = order[j];
+        P->w_eval[j] = weights->w[order[j]];
+        for (int c = 0; c < 3; ++c) P->off_eval[j][c] = off[order[j]][c];
+    }
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "no CUDA device");
+    }
+    *out = P;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
+    if (!P) return STENCIL_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->device);
+    cudaDeviceSynchronize();
+    cudaFree(P->ws);
+    cudaFree(P->hws[0]);
+    cudaFree(P->hws[1]);
+    cudaFree(P->d_status);
+    cudaFree(P->adj_ws);
+    cudaFree(P->adj_partials);
+    cudaSetDevice(cur);
+    delete P;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_set_k(stencil_plan_t P, int32_t k) {
+    if (!P || k < 0) { set_error("invalid plan or k"); return STENCIL_ERR_INVALID_ARG; }
+    const int km = fused_max_k(*P);
+    if (k > std::max(km, 1)) {
+        set_error("k=" + std::to_string(k) + " exceeds this plan's limit " + std::to_string(std::max(km, 1)));
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    P->k = k;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_get_k(stencil_plan_t P, int32_t *k) {
+    if (!P || !k) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *k = uses_fused(P) ? effective_k(P) : 1;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_max_k(stencil_plan_t P, int32_t *kmax) {
+    if (!P || !kmax) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *kmax = std::max(fused_max_k(*P), 1);
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
+    if (!P || (variant != STENCIL_VARIANT_FUSED && variant != STENCIL_VARIANT_PLAIN)) {
+        set_error("invalid plan or variant");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    P->variant = variant;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_launch_count(stencil_plan_t P, int64_t T, int64_t *launches) {
+    if (!P || !launches || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    if (T == 0) { *launches = 0; return STENCIL_OK; }
+    if (!uses_fused(P)) { *launches = T; return STENCIL_OK; }
+    const int k = effective_k(P);
+    *launches = (T + k - 1) / k;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_describe(stencil_plan_t P, char *buf, int32_t len) {
+    if (!P || !buf || len < 1) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    std::string s = uses_fused(P) ? fused_describe(*P, effective_k(P)) : std::string("plain(one step per launch)");
+    strncpy(buf, s.c_str(), (size_t)len - 1);
+    buf[len - 1] = 0;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_run(stencil_plan_t P, const void *u_in, void *u_out, int64_t T, void *stream) {
+    if (!P || !u_in || !u_out || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    const char *a = static_cast<const char *>(u_in);
+    const char *b = static_cast<const char *>(u_out);
+    if (a < b + P->grid_bytes && b < a + P->grid_bytes) {
+        set_error("u_out must not overlap u_in");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        cudaError_t e = cudaMemcpyAsync(u_out, u_in, P->grid_bytes, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaMemcpyAsync");
+    }
+    stencil_status_t s = ensure_status_word(P);
+    if (s != STENCIL_OK) return s;
+    const bool fused = uses_fused(P);
+    const int k = fused ? effective_k(P) : 1;
+    const int64_t passes = (T + k - 1) / k;
+    if (passes > 1) {
+        s = ensure_buf(&P->ws, P->grid_bytes);
+        if (s != STENCIL_OK) return s;
+    }
+    const void *src = u_in;
+    for (int64_t p = 0; p < passes; ++p) {
+        // the last pass lands in u_out; earlier ones alternate ws / u_out
+        void *dst = ((passes - 1 - p) % 2 == 0) ? u_out : P->ws;
+        const int kp = (int)std::min<int64_t>(k, T - p * k);
+        cudaError_t e = fused ? launch_fused(*P, src, dst, kp, st) : launch_plain(*P, src, dst, st);
+        if (e != cudaSuccess) return cuda_fail(e, fused ? "fused kernel launch" : "plain kernel launch");
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_run_host(stencil_plan_t P, const void *h_in, void *h_out, int64_t T, void *stream) {
+    if (!P || !h_in || !h_out || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    stencil_status_t s = ensure_buf(&P->hws[0], P->grid_bytes);
+    if (s == STENCIL_OK) s = ensure_buf(&P->hws[1], P->grid_bytes);
+    if (s != STENCIL_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(P->hws[0], h_in, P->grid_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    s = stencil_run(P, P->hws[0], P->hws[1], T, stream);
+    if (s != STENCIL_OK) return s;
+    e = cudaMemcpyAsync(h_out, P->hws[1], P->grid_bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, int32_t *best_k, double *best_ms) {
+    if (!P || T < 1) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    const int km = fused_max_k(*P);
+    if (km <= 0 || P->variant != STENCIL_VARIANT_FUSED) {
+        if (best_k) *best_k = 1;
+        if (best_ms) *best_ms = -1.0;
+        return STENCIL_OK;
+    }
+    stencil_status_t s = ensure_buf(&P->hws[0], P->grid_bytes);
+    if (s == STENCIL_OK) s = ensure_buf(&P->hws[1], P->grid_bytes);
+    if (s != STENCIL_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(P->hws[0], 0, P->grid_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved = P->k;
+    int bk = 1;
+    float bms = 1e30f;
+    for (int k = 1; k <= km; ++k) {
+        P->k = k;
+        s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
+        if (s != STENCIL_OK) break;
+        float best_rep = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            s = stencil_run(P, P->hws[0], P->hws[1], T, stream);
+            cudaEventRecord(e1, st);
+            if (s != STENCIL_OK) break;
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { s = cuda_fail(e, "tuning run"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_rep = std::min(best_rep, ms);
+        }
+        if (s != STENCIL_OK) break;
+        if (best_rep < bms) { bms = best_rep; bk = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != STENCIL_OK) { P->k = saved; return s; }
+    P->k = bk;
+    if (best_k) *best_k = bk;
+    if (best_ms) *best_ms = bms;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_get_device_status(stencil_plan_t P) {
+    if (!P) { set_error("null plan"); return STENCIL_ERR_INVALID_ARG; }
+    if (!P->d_status) return STENCIL_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, P->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (h != 0) {
+        cudaMemset(P->d_status, 0, sizeof(int));
+        set_error("a device-side bounded wait gave up");
+        return (stencil_status_t)h;
+    }
+    return STENCIL_OK;
+}
+
+}  // extern "C"

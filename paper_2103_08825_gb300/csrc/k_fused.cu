@@ -1,0 +1,83 @@
+// k_fused.cu -- dispatch of one fused pass (k time steps) to the kernel for
+// the plan's dimension and storage type.
+#include <string>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace sg {
+
+#define SG_DECL_F2(DT)                                                                              \
+    cudaError_t launch_f2_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);   \
+    int f2_kmax_##DT(int r);                                                                        \
+    int f2_bw_##DT(int r, int k);
+SG_DECL_F2(F32)
+SG_DECL_F2(F64)
+SG_DECL_F2(BF16)
+SG_DECL_F2(F16)
+SG_DECL_F2(I32)
+#undef SG_DECL_F2
+
+int fused2d_max_k(const stencil_plan_s &P) {
+    if (P.dim != 2 || P.r > 2) return 0;
+    switch (P.dtype) {
+        case STENCIL_F32: return f2_kmax_F32(P.r);
+        case STENCIL_F64: return f2_kmax_F64(P.r);
+        case STENCIL_BF16: return f2_kmax_BF16(P.r);
+        case STENCIL_F16: return f2_kmax_F16(P.r);
+        case STENCIL_I32: return f2_kmax_I32(P.r);
+    }
+    return 0;
+}
+
+cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    switch (P.dtype) {
+        case STENCIL_F32: return launch_f2_F32(P, src, dst, k, st);
+        case STENCIL_F64: return launch_f2_F64(P, src, dst, k, st);
+        case STENCIL_BF16: return launch_f2_BF16(P, src, dst, k, st);
+        case STENCIL_F16: return launch_f2_F16(P, src, dst, k, st);
+        case STENCIL_I32: return launch_f2_I32(P, src, dst, k, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+std::string fused2d_describe(const stencil_plan_s &P, int k) {
+    int bw = 0;
+    switch (P.dtype) {
+        case STENCIL_F32: bw = f2_bw_F32(P.r, k); break;
+        case STENCIL_F64: bw = f2_bw_F64(P.r, k); break;
+        case STENCIL_BF16: bw = f2_bw_BF16(P.r, k); break;
+        case STENCIL_F16: bw = f2_bw_F16(P.r, k); break;
+        case STENCIL_I32: bw = f2_bw_I32(P.r, k); break;
+    }
+    return "fused2d(warp-streamed rows, k=" + std::to_string(k) + ", band=" + std::to_string(bw) + " cols)";
+}
+
+int fused_max_k(const stencil_plan_s &P) {
+    switch (P.dim) {
+        case 1: return fused1d_max_k(P);
+        case 2: return fused2d_max_k(P);
+        case 3: return fused3d_max_k(P);
+    }
+    return 0;
+}
+
+cudaError_t launch_fused(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    switch (P.dim) {
+        case 1: return launch_fused1d(P, src, dst, k, st);
+        case 2: return launch_fused2d(P, src, dst, k, st);
+        case 3: return launch_fused3d(P, src, dst, k, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+std::string fused_describe(const stencil_plan_s &P, int k) {
+    switch (P.dim) {
+        case 1: return fused1d_describe(P, k);
+        case 2: return fused2d_describe(P, k);
+        case 3: return fused3d_describe(P, k);
+    }
+    return "none";
+}
+
+}  // namespace sg

@@ -1,0 +1,479 @@
+// k_fused2d.cuh -- 2D Jacobi sweep with K time steps fused per pass.
+//
+// GPU counterpart of the paper's time-loop unroll-and-jam (Section 3.3,
+// Algorithm 1).  There, vector sets stream along the grid and each is
+// advanced k time levels before it is stored, the older levels kept in
+// registers ("vrl") so that Jacobi semantics hold.  Here one warp streams the
+// rows of a column band: every incoming row at level s contributes to 2r
+// partial rows of level s+1 held in registers; the row that receives its last
+// contribution is complete, is emitted as the incoming row of level s+1, and
+// after K levels it is stored.  Each value is read from HBM once and written
+// once per pass, so the bytes per point update drop by K.
+//
+//   lanes     32 lanes x V contiguous elements = a W-wide window; x-neighbours
+//             across lanes come from warp shuffles (the analogue of the
+//             paper's Assemble, Section 3.2); the window's outer H >= rK
+//             columns are halo, recomputed redundantly (overlapped tiling);
+//   rows      a job covers Ly output rows and reads rK halo rows each side;
+//   input     PROD_TMA: lane 0 streams 8-row x W tiles by TMA
+//             (cp.async.bulk.tensor) into a 3-stage shared-memory ring per
+//             warp, completion tracked by mbarriers (bounded waits; a timeout
+//             sets the status word).  Out-of-range rows/columns are
+//             zero-filled by TMA and then replaced by the Dirichlet value.
+//             PROD_REG: each lane loads its own V elements of the row four
+//             rows ahead into registers, wrapping indices (periodic grids and
+//             rows that are not 16-byte aligned);
+//   boundary  Dirichlet cells outside the domain are reset to the boundary
+//             value at every level (they are never computed);
+//   order     each output is one multiply then FMAs over the offsets in
+//             lexicographic (o_y, o_x) order, the same order as the plain
+//             kernel, so every K gives bit-identical FP32/FP64 results.
+#pragma once
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace sg {
+
+constexpr int F2_NW = 4;       // warps per CTA (independent jobs)
+constexpr int F2_ROWS = 8;     // rows per TMA stage
+constexpr int F2_STAGES = 3;   // TMA ring depth per warp
+constexpr int F2_PREF = 4;     // rows prefetched in registers (PROD_REG)
+constexpr int F2_U = 4;        // step unroll: multiple of 2R (R <= 2) and of F2_PREF
+enum { PROD_TMA = 0, PROD_REG = 1 };
+
+template <int DT, int R, int K> struct F2Geo {
+    using S = typename Traits<DT>::S;
+    static constexpr int V = Traits<DT>::V;
+    static constexpr int W = 32 * V;
+    static constexpr int AL = max_c(align_elems<DT>(), V);
+    static constexpr int H = round_up_c(R * K, AL);
+    static constexpr int BW = W - 2 * H;
+    static constexpr int STAGE_ELEMS = F2_ROWS * W;
+    static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(S);
+    static constexpr int WARP_SMEM = F2_STAGES * STAGE_BYTES;
+    static constexpr int SMEM = F2_NW * WARP_SMEM + F2_NW * F2_STAGES * 8;
+    static_assert(BW >= V, "fusion depth too large for the window");
+    static_assert(R <= V, "x-halo must come from the neighbouring lane");
+};
+
+template <typename C> struct F2Params {
+    GridGeom<C> g;     // n0 = 1, n1 = ny, n2 = nx
+    const void *src;
+    void *dst;
+    int64_t jobs;
+    int64_t bands;
+    int64_t Ly;
+    int vec_ok;        // rows and both base pointers allow V-wide vector access
+    int *status;
+    C w[25];           // evaluation order; up to the r = 2 box
+};
+
+// ------------------------------------------------------------ memory helpers
+template <bool COH, typename T> __device__ __forceinline__ T ldx(const T *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// V contiguous storage elements (16 or 8 bytes) -> arithmetic values
+template <int DT, bool COH>
+__device__ __forceinline__ void ldvec(const typename Traits<DT>::S *p, typename Traits<DT>::C *out) {
+    using S = typename Traits<DT>::S;
+    constexpr int V = Traits<DT>::V;
+    constexpr int BYTES = V * (int)sizeof(S);
+    if constexpr (BYTES == 16) {
+        uint4 v = ldx<COH>(reinterpret_cast<const uint4 *>(p));
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = to_c(s[i]);
+    } else {
+        static_assert(BYTES == 8, "vector width");
+        uint2 v = ldx<COH>(reinterpret_cast<const uint2 *>(p));
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = to_c(s[i]);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void stvec(typename Traits<DT>::S *p, const typename Traits<DT>::C *in) {
+    using S = typename Traits<DT>::S;
+    constexpr int V = Traits<DT>::V;
+    constexpr int BYTES = V * (int)sizeof(S);
+    S tmp[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) tmp[i] = from_c<S>(in[i]);
+    if constexpr (BYTES == 16) *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(tmp);
+    else *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(tmp);
+}
+
+template <int DT>
+__device__ __forceinline__ void ldsvec(const typename Traits<DT>::S *p, typename Traits<DT>::C *out) {
+    using S = typename Traits<DT>::S;
+    constexpr int V = Traits<DT>::V;
+    constexpr int BYTES = V * (int)sizeof(S);
+    if constexpr (BYTES == 16) {
+        uint4 v = *reinterpret_cast<const uint4 *>(p);
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = to_c(s[i]);
+    } else {
+        uint2 v = *reinterpret_cast<const uint2 *>(p);
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = to_c(s[i]);
+    }
+}
+
+// One lane's V elements of virtual row y, columns xl..xl+V-1, through the
+// boundary rule (PROD_REG input path).
+template <int DT, bool COH>
+__device__ __forceinline__ void load_row_reg(const typename Traits<DT>::S *__restrict__ src, int64_t nx, int64_t ny,
+                                             bool periodic, typename Traits<DT>::C bval, int64_t y, int64_t xl,
+                                             bool vec_ok, typename Traits<DT>::C *out) {
+    constexpr int V = Traits<DT>::V;
+    if (y < 0 || y >= ny) {
+        if (!periodic) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = bval;
+            return;
+        }
+        y = wrap_idx(y, ny);
+    }
+    const typename Traits<DT>::S *row = src + y * nx;
+    if (vec_ok && xl >= 0 && xl + V <= nx) {
+        ldvec<DT, COH>(row + xl, out);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            int64_t x = xl + v;
+            if (x >= 0 && x < nx) out[v] = to_c(ldx<COH>(row + x));
+            else if (periodic) out[v] = to_c(ldx<COH>(row + wrap_idx(x, nx)));
+            else out[v] = bval;
+        }
+    }
+}
+
+// ------------------------------------------------------------- one job
+// Advances the rows [yo0, yo1) x columns [xo0, xo0 + BW) of one grid by K
+// steps.  Returns false if a bounded wait gave up (caller records status).
+template <int DT, int R, int PAT, int K, int PROD, bool COH>
+__device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typename Traits<DT>::S *__restrict__ src,
+                                            typename Traits<DT>::S *__restrict__ dst, int64_t nx, int64_t ny,
+                                            bool dir, typename Traits<DT>::C bval, const typename Traits<DT>::C *wr,
+                                            int64_t xo0, int64_t yo0, int64_t yo1, bool vec_ok,
+                                            typename Traits<DT>::S *stg, uint64_t *bars, uint32_t &gst, int lane) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F2Geo<DT, R, K>;
+    using Sh = Shape<2, R, PAT>;
+    constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, NS = 2 * R;
+    constexpr uint32_t FULLM = (1u << V) - 1u;
+
+    const int64_t xw0 = xo0 - H;
+    const int64_t xl = xw0 + (int64_t)lane * V;
+    const int64_t yi0 = yo0 - (int64_t)R * K;
+    const int nsteps = (int)(yo1 - yo0) + 2 * R * K;
+    const int nsp = round_up_c(nsteps, F2_U);
+    uint32_t cmask = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (xl + v >= 0 && xl + v < nx) cmask |= 1u << v;
+    const bool need_cmask = dir && __any_sync(0xffffffffu, cmask != FULLM);
+    const bool lane_out = (lane * V >= H) && (lane * V < H + BW);
+
+    int nst = 0;
+    C ring[F2_PREF][V];
+    if constexpr (PROD == PROD_TMA) {
+        nst = (nsp + F2_ROWS - 1) / F2_ROWS;
+        __syncwarp();   // every lane is done with the previous job's stages
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            const int pre = nst < F2_STAGES ? nst : F2_STAGES;
+            for (int q = 0; q < pre; ++q) {
+                const uint32_t g = gst + q, slot = g % F2_STAGES;
+                mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
+                tma_load_2d(stg + slot * G::STAGE_ELEMS, tmap, &bars[slot], (int)xw0, (int)(yi0 + q * F2_ROWS));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < F2_PREF; ++q)
+            load_row_reg<DT, COH>(src, nx, ny, !dir, bval, yi0 + q, xl, vec_ok, ring[q]);
+    }
+
+    C P[K][NS][V];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int m = 0; m < NS; ++m)
+#pragma unroll
+            for (int v = 0; v < V; ++v) P[s][m][v] = C(0);
+
+    for (int i0 = 0; i0 < nsp; i0 += F2_U) {
+#pragma unroll
+        for (int ph = 0; ph < F2_U; ++ph) {
+            const int i = i0 + ph;
+            const int64_t yin = yi0 + i;
+            C cur[V];
+            int q = 0, rr = 0;
+            if constexpr (PROD == PROD_TMA) {
+                q = i / F2_ROWS;
+                rr = i - q * F2_ROWS;
+                const uint32_t g = gst + q, slot = g % F2_STAGES;
+                if (rr == 0) {
+                    const bool ok = mbar_wait_bounded(&bars[slot], (g / F2_STAGES) & 1u);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        // give up: wait (bounded) for this warp's copies in flight
+                        if (lane == 0)
+                            for (int qq = q; qq < nst && qq < q + F2_STAGES; ++qq) {
+                                const uint32_t gg = gst + qq;
+                                mbar_wait_bounded(&bars[gg % F2_STAGES], (gg / F2_STAGES) & 1u);
+                            }
+                        __syncwarp();
+                        return false;
+                    }
+                }
+                ldsvec<DT>(stg + slot * G::STAGE_ELEMS + rr * W + lane * V, cur);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) cur[v] = ring[ph % F2_PREF][v];
+                load_row_reg<DT, COH>(src, nx, ny, !dir, bval, yin + F2_PREF, xl, vec_ok, ring[ph % F2_PREF]);
+            }
+            if (dir) {
+                if (yin < 0 || yin >= ny) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) cur[v] = bval;
+                } else if (need_cmask) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (!((cmask >> v) & 1u)) cur[v] = bval;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                // cur: level-s row J = yin - sR.  Partial rows of level s+1:
+                // Y = J - R + m sits in slot (ph + m) % NS.
+                C ext[V + 2 * R];
+#pragma unroll
+                for (int v = 0; v < V; ++v) ext[R + v] = cur[v];
+#pragma unroll
+                for (int qq = 0; qq < R; ++qq) {
+                    ext[R - 1 - qq] = __shfl_up_sync(0xffffffffu, cur[V - 1 - qq], 1);
+                    ext[R + V + qq] = __shfl_down_sync(0xffffffffu, cur[qq], 1);
+                }
+                C emit[V];
+                const int s0 = ph % NS;
+                // complete Y = J - R with its o_y = +R terms
+#pragma unroll
+                for (int v = 0; v < V; ++v) emit[v] = P[s][s0][v];
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    if (!Sh::inc(0, R, ox)) continue;
+                    const C w = wr[Sh::widx(0, R, ox)];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) emit[v] = op_fma(w, ext[R + v + ox], emit[v]);
+                }
+                // rows Y = J - R + m (0 < m < 2R) take their o_y = R - m terms
+#pragma unroll
+                for (int m = 1; m < NS; ++m) {
+                    const int oy = R - m;
+                    const int sl = (ph + m) % NS;
+#pragma unroll
+                    for (int ox = -R; ox <= R; ++ox) {
+                        if (!Sh::inc(0, oy, ox)) continue;
+                        const C w = wr[Sh::widx(0, oy, ox)];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) P[s][sl][v] = op_fma(w, ext[R + v + ox], P[s][sl][v]);
+                    }
+                }
+                // start Y = J + R with its o_y = -R terms (first term: multiply)
+                {
+                    bool first = true;
+#pragma unroll
+                    for (int ox = -R; ox <= R; ++ox) {
+                        if (!Sh::inc(0, -R, ox)) continue;
+                        const C w = wr[Sh::widx(0, -R, ox)];
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            P[s][s0][v] = first ? op_mul(w, ext[R + v + ox]) : op_fma(w, ext[R + v + ox], P[s][s0][v]);
+                        first = false;
+                    }
+                }
+                // emitted row Y = yin - (s+1)R: Dirichlet cells keep the boundary value
+                if (dir) {
+                    const int64_t ye = yin - (int64_t)(s + 1) * R;
+                    if (ye < 0 || ye >= ny) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) emit[v] = bval;
+                    } else if (need_cmask) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            if (!((cmask >> v) & 1u)) emit[v] = bval;
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) cur[v] = emit[v];
+            }
+            // level-K row
+            const int64_t yout = yin - (int64_t)K * R;
+            if (yout >= yo0 && yout < yo1 && lane_out) {
+                S *rowp = dst + yout * nx;
+                if (vec_ok && xl + V <= nx) {
+                    stvec<DT>(rowp + xl, cur);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (xl + v < nx) rowp[xl + v] = from_c<S>(cur[v]);
+                }
+            }
+            if constexpr (PROD == PROD_TMA) {
+                if (rr == F2_ROWS - 1) {
+                    // stage consumed by every lane: refill it with the stage S ahead
+                    __syncwarp();
+                    if (lane == 0 && q + F2_STAGES < nst) {
+                        fence_proxy_async_smem();
+                        const uint32_t g = gst + q + F2_STAGES, slot = g % F2_STAGES;
+                        mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
+                        tma_load_2d(stg + slot * G::STAGE_ELEMS, tmap, &bars[slot], (int)xw0,
+                                    (int)(yi0 + (q + F2_STAGES) * F2_ROWS));
+                    }
+                }
+            }
+        }
+    }
+    gst += (uint32_t)nst;
+    return true;
+}
+
+template <int DT, int R, int PAT, int K, int PROD>
+__global__ void __launch_bounds__(F2_NW * 32)
+    fused2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F2Params<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F2Geo<DT, R, K>;
+    using Sh = Shape<2, R, PAT>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S *stg = reinterpret_cast<S *>(smem + warp * G::WARP_SMEM);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F2_NW * G::WARP_SMEM) + warp * F2_STAGES;
+    if constexpr (PROD == PROD_TMA) {
+        if (lane == 0) {
+            for (int s = 0; s < F2_STAGES; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+            prefetch_tmap(&tmap);
+        }
+        __syncwarp();
+    }
+    C wr[Sh::npts];
+#pragma unroll
+    for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
+    const bool dir = p.g.bkind == STENCIL_DIRICHLET;
+    uint32_t gst = 0;
+    for (int64_t job = (int64_t)blockIdx.x * F2_NW + warp; job < p.jobs; job += (int64_t)gridDim.x * F2_NW) {
+        const int64_t band = job % p.bands, chunk = job / p.bands;
+        const int64_t yo0 = chunk * p.Ly;
+        const int64_t yo1 = yo0 + p.Ly < p.g.n1 ? yo0 + p.Ly : p.g.n1;
+        const bool ok = fused2d_job<DT, R, PAT, K, PROD, false>(
+            &tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), p.g.n2, p.g.n1, dir, p.g.bval, wr,
+            band * G::BW, yo0, yo1, p.vec_ok != 0, stg, bars, gst, lane);
+        if (!ok) {
+            if (lane == 0) record_status(p.status, kStatusTimeout);
+            return;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename C> C conv_w(double w) {
+    if constexpr (sizeof(C) == 4 && C(-1) > C(0)) return (C)(uint32_t)(int64_t)w;
+    else return (C)w;
+}
+
+template <int DT, int R, int PAT, int K>
+cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F2Geo<DT, R, K>;
+    F2Params<C> p;
+    p.g.n0 = 1;
+    p.g.n1 = P.n[1];
+    p.g.n2 = P.n[2];
+    p.g.bkind = P.bkind;
+    p.g.bval = conv_w<C>(P.bval);
+    p.src = src;
+    p.dst = dst;
+    p.status = P.d_status;
+    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
+    const int64_t nx = P.n[2], ny = P.n[1];
+    p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+    bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && ((uintptr_t)src % 16 == 0) &&
+               nx < (1ll << 31) && ny < (1ll << 31);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (tma) {
+        const int64_t dims[2] = {nx, ny};
+        const uint32_t box[2] = {(uint32_t)G::W, (uint32_t)F2_ROWS};
+        tma = make_tmap(&map, DT, 2, dims, box, src);
+    }
+    auto kern = tma ? fused2d_kernel<DT, R, PAT, K, PROD_TMA> : fused2d_kernel<DT, R, PAT, K, PROD_REG>;
+    const int smem = tma ? G::SMEM : 0;
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[tma ? 0 : 1]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done[tma ? 0 : 1] = true;
+    }
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F2_NW * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    const int64_t bands = (nx + G::BW - 1) / G::BW;
+    const int64_t slots = (int64_t)P.sm_count * bps * F2_NW;
+    const int64_t min_ly = 4 * R * K > 16 ? 4 * R * K : 16;
+    int64_t chunks = slots / bands;
+    if (chunks < 1) chunks = 1;
+    const int64_t max_chunks = ny / min_ly > 1 ? ny / min_ly : 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    p.Ly = (ny + chunks - 1) / chunks;
+    chunks = (ny + p.Ly - 1) / p.Ly;
+    p.bands = bands;
+    p.jobs = bands * chunks;
+    int64_t grid = (p.jobs + F2_NW - 1) / F2_NW;
+    if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;
+    kern<<<(unsigned)grid, F2_NW * 32, smem, st>>>(map, p);
+    return cudaGetLastError();
+}
+
+// Largest K instantiated for (dtype, r) -- bounded by register pressure.
+template <int DT> constexpr int f2_kmax(int r) {
+    return Traits<DT>::V == 2 ? (r == 1 ? 4 : 2) : (r == 1 ? 8 : 4);
+}
+
+template <int DT, int R, int PAT>
+cudaError_t launch_f2_k(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    constexpr int KM = f2_kmax<DT>(R);
+    switch (k) {
+        case 1: return launch_f2_t<DT, R, PAT, 1>(P, src, dst, st);
+        case 2: return launch_f2_t<DT, R, PAT, 2>(P, src, dst, st);
+        case 3: if constexpr (KM >= 3) return launch_f2_t<DT, R, PAT, 3>(P, src, dst, st); break;
+        case 4: if constexpr (KM >= 4) return launch_f2_t<DT, R, PAT, 4>(P, src, dst, st); break;
+        case 5: if constexpr (KM >= 5) return launch_f2_t<DT, R, PAT, 5>(P, src, dst, st); break;
+        case 6: if constexpr (KM >= 6) return launch_f2_t<DT, R, PAT, 6>(P, src, dst, st); break;
+        case 7: if constexpr (KM >= 7) return launch_f2_t<DT, R, PAT, 7>(P, src, dst, st); break;
+        case 8: if constexpr (KM >= 8) return launch_f2_t<DT, R, PAT, 8>(P, src, dst, st); break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int DT>
+cudaError_t launch_f2_dt(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    const bool box = P.pattern == STENCIL_BOX;
+    if (P.r == 1) return box ? launch_f2_k<DT, 1, STENCIL_BOX>(P, src, dst, k, st)
+                             : launch_f2_k<DT, 1, STENCIL_STAR>(P, src, dst, k, st);
+    if (P.r == 2) return box ? launch_f2_k<DT, 2, STENCIL_BOX>(P, src, dst, k, st)
+                             : launch_f2_k<DT, 2, STENCIL_STAR>(P, src, dst, k, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sg

@@ -1,0 +1,21 @@
+// k_fused2d_f32.cu -- instantiations of the 2D fused kernel for STENCIL_F32
+// storage (one translation unit per dtype keeps the build parallel).
+#include "k_fused2d.cuh"
+
+namespace sg {
+cudaError_t launch_f2_F32(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    return launch_f2_dt<STENCIL_F32>(P, src, dst, k, st);
+}
+int f2_kmax_F32(int r) { return f2_kmax<STENCIL_F32>(r); }
+int f2_bw_F32(int r, int k) {
+    switch (k) {
+        case 1: return r == 1 ? F2Geo<STENCIL_F32, 1, 1>::BW : F2Geo<STENCIL_F32, 2, 1>::BW;
+        case 2: return r == 1 ? F2Geo<STENCIL_F32, 1, 2>::BW : F2Geo<STENCIL_F32, 2, 2>::BW;
+        default: {
+            int v = Traits<STENCIL_F32>::V, w = 32 * v, al = align_elems<STENCIL_F32>() > v ? align_elems<STENCIL_F32>() : v;
+            int h = (r * k + al - 1) / al * al;
+            return w - 2 * h;
+        }
+    }
+}
+}  // namespace sg

@@ -1,0 +1,21 @@
+// k_fused2d_i32.cu -- instantiations of the 2D fused kernel for STENCIL_I32
+// storage (one translation unit per dtype keeps the build parallel).
+#include "k_fused2d.cuh"
+
+namespace sg {
+cudaError_t launch_f2_I32(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    return launch_f2_dt<STENCIL_I32>(P, src, dst, k, st);
+}
+int f2_kmax_I32(int r) { return f2_kmax<STENCIL_I32>(r); }
+int f2_bw_I32(int r, int k) {
+    switch (k) {
+        case 1: return r == 1 ? F2Geo<STENCIL_I32, 1, 1>::BW : F2Geo<STENCIL_I32, 2, 1>::BW;
+        case 2: return r == 1 ? F2Geo<STENCIL_I32, 1, 2>::BW : F2Geo<STENCIL_I32, 2, 2>::BW;
+        default: {
+            int v = Traits<STENCIL_I32>::V, w = 32 * v, al = align_elems<STENCIL_I32>() > v ? align_elems<STENCIL_I32>() : v;
+            int h = (r * k + al - 1) / al * al;
+            return w - 2 * h;
+        }
+    }
+}
+}  // namespace sg

@@ -1,0 +1,207 @@
+// k_plain.cu -- one Jacobi step per launch (the plain GPU sweep).
+//
+// Every thread produces 4 consecutive points of one x-row.  For each row
+// offset (o_0, o_1) it reads the span of the source row it needs (x-halo of
+// r only for the rows where the pattern has x-offsets), straight from HBM/L2
+// through the read-only path, then accumulates the offsets in lexicographic
+// order (paper, Section 1: the point update is a weighted sum of neighbours
+// at the previous time level).  This is the GPU analogue of the paper's
+// "multiple load" vectorisation (Section 2.1): each output loads all of its
+// own inputs, and neighbour reuse is left to the caches.
+#include "common.cuh"
+#include "plan.h"
+
+namespace sg {
+
+template <typename S, typename C>
+__device__ __forceinline__ void ldg4(const S *p, C out[4]) {
+    if constexpr (sizeof(S) == 4) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = to_c(s[i]);
+    } else if constexpr (sizeof(S) == 8) {
+        uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+        uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+        const S *sa = reinterpret_cast<const S *>(&a);
+        const S *sb = reinterpret_cast<const S *>(&b);
+        out[0] = to_c(sa[0]); out[1] = to_c(sa[1]); out[2] = to_c(sb[0]); out[3] = to_c(sb[1]);
+    } else {
+        uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        const S *s = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = to_c(s[i]);
+    }
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void st4(S *p, const C in[4]) {
+    S tmp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tmp[i] = from_c<S>(in[i]);
+    if constexpr (sizeof(S) == 4) {
+        *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(tmp);
+    } else if constexpr (sizeof(S) == 8) {
+        reinterpret_cast<uint4 *>(p)[0] = reinterpret_cast<const uint4 *>(tmp)[0];
+        reinterpret_cast<uint4 *>(p)[1] = reinterpret_cast<const uint4 *>(tmp)[1];
+    } else {
+        *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(tmp);
+    }
+}
+
+template <int DT, int D, int R, int PAT>
+__global__ void __launch_bounds__(256) plain_kernel(const PlainParams<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using Sh = Shape<D, R, PAT>;
+    constexpr int VX = 4;
+    const S *__restrict__ src = static_cast<const S *>(p.src);
+    S *__restrict__ dst = static_cast<S *>(p.dst);
+    const int64_t n0 = p.g.n0, n1 = p.g.n1, n2 = p.g.n2;
+    const bool periodic = p.g.bkind == STENCIL_PERIODIC;
+    const C bval = p.g.bval;
+    const int64_t groups = (n2 + VX - 1) / VX;
+    const int64_t total = n0 * n1 * groups;
+
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t % groups, row = t / groups;
+        const int64_t i1 = row % n1, i0 = row / n1;
+        const int64_t x0 = g * VX;
+        const bool x_inner = (x0 - R >= 0) && (x0 + VX + R <= n2);
+        C acc[VX];
+        bool first = true;
+#pragma unroll
+        for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz) {
+#pragma unroll
+            for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy) {
+                if (!Sh::inc(oz, oy, 0) && !(PAT == STENCIL_BOX)) continue;
+                const bool halo = (PAT == STENCIL_BOX) || (oz == 0 && oy == 0);
+                int64_t r0 = i0 + oz, r1 = i1 + oy;
+                bool row_ok = true;
+                if (r0 < 0 || r0 >= n0) { if (periodic) r0 = wrap_idx(r0, n0); else row_ok = false; }
+                if (r1 < 0 || r1 >= n1) { if (periodic) r1 = wrap_idx(r1, n1); else row_ok = false; }
+                const S *rowp = src + (r0 * n1 + r1) * n2;
+                C span[VX + 2 * R];
+                if (!row_ok) {
+#pragma unroll
+                    for (int q = 0; q < VX + 2 * R; ++q) span[q] = bval;
+                } else if (x_inner) {
+                    if (p.vec_ok) {
+                        ldg4<S, C>(rowp + x0, span + R);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < VX; ++q) span[R + q] = to_c(__ldg(rowp + x0 + q));
+                    }
+                    if (halo) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            span[q] = to_c(__ldg(rowp + x0 - R + q));
+                            span[R + VX + q] = to_c(__ldg(rowp + x0 + VX + q));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VX + 2 * R; ++q) {
+                        if (!halo && (q < R || q >= R + VX)) continue;
+                        int64_t x = x0 - R + q;
+                        if (x >= 0 && x < n2) span[q] = to_c(__ldg(rowp + x));
+                        else if (periodic) span[q] = to_c(__ldg(rowp + wrap_idx(x, n2)));
+                        else span[q] = bval;
+                    }
+                }
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    if (!Sh::inc(oz, oy, ox)) continue;
+                    const C w = p.w[Sh::widx(oz, oy, ox)];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v)
+                        acc[v] = first ? op_mul(w, span[R + v + ox]) : op_fma(w, span[R + v + ox], acc[v]);
+                    first = false;
+                }
+            }
+        }
+        S *out = dst + (i0 * n1 + i1) * n2;
+        if (p.vec_ok && x0 + VX <= n2) {
+            st4<S, C>(out + x0, acc);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v)
+                if (x0 + v < n2) out[x0 + v] = from_c<S>(acc[v]);
+        }
+    }
+}
+
+template <typename C>
+static void fill_geom(const stencil_plan_s &P, GridGeom<C> &g) {
+    g.n0 = P.n[0];
+    g.n1 = P.n[1];
+    g.n2 = P.n[2];
+    g.bkind = P.bkind;
+    if constexpr (sizeof(C) == 4 && C(-1) > C(0)) {
+        g.bval = (C)(uint32_t)(int64_t)P.bval;
+    } else {
+        g.bval = (C)P.bval;
+    }
+}
+
+template <typename C>
+static C conv_weight(double w) {
+    if constexpr (sizeof(C) == 4 && C(-1) > C(0)) return (C)(uint32_t)(int64_t)w;  // uint32
+    else return (C)w;
+}
+
+template <int DT, int D, int R, int PAT>
+static cudaError_t launch_plain_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    using C = typename Traits<DT>::C;
+    PlainParams<C> p;
+    fill_geom<C>(P, p.g);
+    p.src = src;
+    p.dst = dst;
+    p.np = P.np;
+    p.vec_ok = (P.n[2] % 4 == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+    for (int j = 0; j < P.np; ++j) p.w[j] = conv_weight<C>(P.w_eval[j]);
+    const int64_t total = P.n[0] * P.n[1] * ((P.n[2] + 3) / 4);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > (int64_t)P.sm_count * 64) blocks = (int64_t)P.sm_count * 64;
+    if (blocks < 1) blocks = 1;
+    plain_kernel<DT, D, R, PAT><<<(unsigned)blocks, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int DT, int D>
+static cudaError_t dispatch_r(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    const bool box = P.pattern == STENCIL_BOX;
+    switch (P.r) {
+        case 1: return box ? launch_plain_t<DT, D, 1, STENCIL_BOX>(P, src, dst, st)
+                           : launch_plain_t<DT, D, 1, STENCIL_STAR>(P, src, dst, st);
+        case 2: return box ? launch_plain_t<DT, D, 2, STENCIL_BOX>(P, src, dst, st)
+                           : launch_plain_t<DT, D, 2, STENCIL_STAR>(P, src, dst, st);
+        case 3: return box ? launch_plain_t<DT, D, 3, STENCIL_BOX>(P, src, dst, st)
+                           : launch_plain_t<DT, D, 3, STENCIL_STAR>(P, src, dst, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int DT>
+static cudaError_t dispatch_d(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    switch (P.dim) {
+        case 1: return dispatch_r<DT, 1>(P, src, dst, st);
+        case 2: return dispatch_r<DT, 2>(P, src, dst, st);
+        case 3: return dispatch_r<DT, 3>(P, src, dst, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_plain(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    switch (P.dtype) {
+        case STENCIL_F64: return dispatch_d<STENCIL_F64>(P, src, dst, st);
+        case STENCIL_F32: return dispatch_d<STENCIL_F32>(P, src, dst, st);
+        case STENCIL_BF16: return dispatch_d<STENCIL_BF16>(P, src, dst, st);
+        case STENCIL_F16: return dispatch_d<STENCIL_F16>(P, src, dst, st);
+        case STENCIL_I32: return dispatch_d<STENCIL_I32>(P, src, dst, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sg

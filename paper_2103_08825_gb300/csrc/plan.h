@@ -1,0 +1,71 @@
+// plan.h -- host-side plan object and the internal launch interface between
+// the C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/stencil.h"
+
+namespace sg {
+constexpr int kHostMaxPts = 343;
+}
+
+struct stencil_plan_s {
+    int dim = 0, r = 0, pattern = 0, np = 0, dtype = 0, bkind = 0;
+    double bval = 0.0;
+    int64_t n[3] = {1, 1, 1};   // padded to 3D: n[0] outermost, n[2] unit stride
+    int64_t npts = 0;
+    double w_compact[sg::kHostMaxPts] = {};
+    // evaluation (lexicographic) order of the offsets and their weights
+    int off_eval[sg::kHostMaxPts][3] = {};
+    double w_eval[sg::kHostMaxPts] = {};
+    int eval_to_compact[sg::kHostMaxPts] = {};
+    int k = 0;                 // 0 = default
+    int variant = STENCIL_VARIANT_FUSED;
+    int device = 0;
+    int sm_count = 0;
+    void *ws = nullptr;        // one grid: intermediate passes of stencil_run
+    void *hws[2] = {nullptr, nullptr};   // device copies for stencil_run_host
+    size_t grid_bytes = 0;
+    int *d_status = nullptr;   // device status word (0 = OK)
+    // adjoint workspace
+    void *adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
+    double *adj_partials = nullptr;
+    size_t adj_partials_n = 0;
+};
+
+namespace sg {
+
+size_t dtype_size(int dtype);
+
+// one plain Jacobi step: dst = A(src)   (k_plain.cu)
+cudaError_t launch_plain(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st);
+
+// one fused pass of `k` steps (k_fused1d.cu / k_fused2d_*.cu / k_fused3d.cu)
+int fused_max_k(const stencil_plan_s &P);
+cudaError_t launch_fused(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
+std::string fused_describe(const stencil_plan_s &P, int k);
+
+// per-dimension entry points used by launch_fused
+int fused2d_max_k(const stencil_plan_s &P);
+cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
+std::string fused2d_describe(const stencil_plan_s &P, int k);
+int fused3d_max_k(const stencil_plan_s &P);
+cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
+std::string fused3d_describe(const stencil_plan_s &P, int k);
+int fused1d_max_k(const stencil_plan_s &P);
+cudaError_t launch_fused1d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
+std::string fused1d_describe(const stencil_plan_s &P, int k);
+
+// TMA descriptor for a dense row-major grid (box dims innermost first)
+bool make_tmap(CUtensorMap *map, int dtype, int rank, const int64_t *dims_inner_first, const uint32_t *box,
+               const void *base);
+
+void set_error(const std::string &msg);
+
+}  // namespace sg

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA kernels (through the C ABI) against the FP64/uint32
+oracle on the same seeded inputs.
+
+Bars (written here): int32 mode bit-exact; FP64 normwise error <= 1e-12;
+FP32 normwise error <= 1e-5 after T steps; every fusion depth k gives results
+bit-identical to the plain one-step kernel in FP32, FP64 and int32 (same
+per-point operation order); BF16/F16 storage within the bound derived from
+one round-to-nearest per pass (unit roundoff 2^-8 / 2^-11) for positive
+weights summing to <= 1, which keep the max norm non-increasing.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import (BOX, DIRICHLET, PERIODIC, STAR, box_weights, c2_2d5p, c2_2d9p, f32_weights, npoints,
+                   sine_mode_1d, star_weights, uniform01, uniform_u16)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def sgmod():
+    import paper_2103_08825_gb300 as sg
+    sg.load()
+    return sg
+
+
+def gpu_run(plan, u0, T, k=None, variant=0):
+    sg = sgmod()
+    sg.stencil_plan_set_variant(plan, variant)
+    if k is not None:
+        sg.stencil_plan_set_k(plan, k)
+    x = torch.from_numpy(np.ascontiguousarray(u0)).to(DEV)
+    if plan.dtype in (sg.STENCIL_BF16, sg.STENCIL_F16):
+        x = x.to(plan.torch_dtype)
+    y = torch.empty_like(x)
+    sg.stencil_run(plan, x, y, T)
+    torch.cuda.synchronize()
+    assert sg.stencil_get_device_status(plan) == 0
+    return y
+
+
+def normwise(g, o):
+    return float(np.max(np.abs(np.asarray(g, np.float64) - o)) / max(1e-300, np.max(np.abs(o))))
+
+
+def kvalues(plan):
+    return list(range(1, sgmod().stencil_plan_max_k(plan) + 1))
+
+
+SHAPES_2D = [(67, 300), (5, 1), (1, 7), (33, 129), (130, 17)]
+
+
+# ------------------------------------------------------------- int32 mode
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_int32_bit_exact_2d_every_k(pattern, r, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(10 * r + pattern + 3 * bkind)
+    for shape in SHAPES_2D:
+        w = [float(x) for x in rng.integers(-3, 8, npoints(2, r, pattern))]
+        bval = 12345 if bkind == DIRICHLET else 0
+        u0 = uniform_u16(700 + shape[0], shape[0] * shape[1]).reshape(shape)
+        plan = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, bval, sg.STENCIL_I32)
+        for T in (1, 7, 13):
+            ref = oracle.run_int(2, r, pattern, shape, w, bkind, bval, u0, T)
+            got = gpu_run(plan, u0, T, variant=1).cpu().numpy()
+            np.testing.assert_array_equal(got, ref, err_msg=f"plain {shape} T={T}")
+            for k in kvalues(plan):
+                got = gpu_run(plan, u0, T, k=k).cpu().numpy()
+                np.testing.assert_array_equal(got, ref, err_msg=f"fused k={k} {shape} T={T}")
+
+
+@pytest.mark.parametrize("d,shape,r", [(1, (1001,), 1), (1, (3,), 2), (1, (257,), 3), (3, (9, 10, 37), 1),
+                                       (3, (1, 1, 5), 1), (3, (6, 5, 11), 2)])
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_int32_bit_exact_1d_3d(d, shape, r, pattern, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(d + r + pattern + bkind)
+    w = [float(x) for x in rng.integers(-3, 8, npoints(d, r, pattern))]
+    bval = -77 if bkind == DIRICHLET else 0
+    u0 = uniform_u16(900 + d, int(np.prod(shape))).reshape(shape)
+    plan = sg.stencil_plan_create(d, r, shape, pattern, w, bkind, bval, sg.STENCIL_I32)
+    for T in (1, 6):
+        ref = oracle.run_int(d, r, pattern, shape, w, bkind, bval, u0, T)
+        np.testing.assert_array_equal(gpu_run(plan, u0, T, variant=1).cpu().numpy(), ref)
+        for k in kvalues(plan):
+            np.testing.assert_array_equal(gpu_run(plan, u0, T, k=k).cpu().numpy(), ref)
+
+
+# --------------------------------------------------------- floating point
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_f64_f32_2d_against_oracle_and_plain(pattern, r, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(40 + r + pattern + bkind)
+    for shape in [(67, 300), (130, 17), (2, 3)]:
+        w = list(rng.uniform(-0.1, 0.4, npoints(2, r, pattern)))
+        bval = 0.3 if bkind == DIRICHLET else 0.0
+        u0 = uniform01(1002, shape[0] * shape[1]).reshape(shape)
+        T = 13
+        # FP64
+        p64 = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, bval, sg.STENCIL_F64)
+        ref = oracle.run(2, r, pattern, shape, w, bkind, bval, u0, T)
+        base = gpu_run(p64, u0, T, variant=1).cpu().numpy()
+        assert normwise(base, ref) <= 1e-12
+        for k in kvalues(p64):
+            np.testing.assert_array_equal(gpu_run(p64, u0, T, k=k).cpu().numpy(), base)
+        # FP32
+        u32 = u0.astype(np.float32)
+        p32 = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, bval, sg.STENCIL_F32)
+        ref32 = oracle.run(2, r, pattern, shape, f32_weights(w), bkind, float(np.float32(bval)),
+                           u32.astype(np.float64), T)
+        base32 = gpu_run(p32, u32, T, variant=1).cpu().numpy()
+        assert normwise(base32, ref32) <= 1e-5
+        for k in kvalues(p32):
+            np.testing.assert_array_equal(gpu_run(p32, u32, T, k=k).cpu().numpy(), base32, err_msg=f"k={k}")
+
+
+@pytest.mark.parametrize("dt,ur", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+def test_half_storage_error_bound(dt, ur, pattern):
+    sg = sgmod()
+    code = sg.STENCIL_BF16 if dt == "bf16" else sg.STENCIL_F16
+    shape, T = (97, 333), 24
+    w = star_weights(2, 1, 0.5, 0.125) if pattern == STAR else box_weights(2, 1, 1.0 / 9.0)
+    plan = sg.stencil_plan_create(2, 1, shape, pattern, w, DIRICHLET, 0.0, code)
+    u0 = uniform01(1002, shape[0] * shape[1]).reshape(shape).astype(np.float32)
+    x = torch.from_numpy(u0).to(sg.torch_dtype(code))
+    uq = x.float().numpy().astype(np.float64)          # the stored (quantised) input
+    ref = oracle.run(2, 1, pattern, shape, f32_weights(w), DIRICHLET, 0.0, uq, T)
+    for k in kvalues(plan):
+        got = gpu_run(plan, u0, T, k=k)
+        passes = -(-T // k)
+        err = float(np.max(np.abs(got.float().cpu().numpy().astype(np.float64) - ref)))
+        assert err <= (passes * ur + 1e-5) * np.max(np.abs(uq)), (k, err)
+
+
+# ---------------------------------------------------- full-size workloads
+def sample_points(shape, n_random=120, seed=5):
+    ny, nx = shape
+    rng = np.random.default_rng(seed)
+    pts = {(0, 0), (0, nx - 1), (ny - 1, 0), (ny - 1, nx - 1), (ny // 2, 0), (0, nx // 2)}
+    for bw in (120, 112, 124, 104, 96):   # band seams of the fused kernel for k = 1..8
+        for j in (1, 2, 7, nx // bw - 1):
+            for dx in (-1, 0):
+                x = j * bw + dx
+                if 0 <= x < nx:
+                    pts.add((int(rng.integers(0, ny)), x))
+    for y in (1, 2, 63, 64, 65, 127, 128, 129, ny - 2):
+        pts.add((y, int(rng.integers(0, nx))))
+    for _ in range(n_random):
+        pts.add((int(rng.integers(0, ny)), int(rng.integers(0, nx))))
+    return np.array(sorted(pts), dtype=np.int64)
+
+
+@pytest.mark.parametrize("maker", [c2_2d5p, c2_2d9p])
+def test_full_size_2d_fp32_sampled(maker):
+    """8192^2, T=64, FP32, at the plan's default k (the launch configuration
+    the benchmark times): sampled outputs against the oracle's dependency
+    cones, and the whole grid bit-identical to the plain one-step sweep."""
+    sg = sgmod()
+    p = maker()
+    u0 = uniform01(p.seed, p.npts).reshape(p.shape).astype(np.float32)
+    plan = sg.stencil_plan_create(2, 1, p.shape, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_F32)
+    fused = gpu_run(plan, u0, p.T)
+    plain = gpu_run(plan, u0, p.T, variant=1)
+    assert torch.equal(fused, plain)
+    pts = sample_points(p.shape)
+    ref = oracle.points(2, 1, p.pattern, p.shape, f32_weights(p.weights), p.bkind, p.bval,
+                        u0.astype(np.float64), p.T, pts)
+    got = fused.cpu().numpy()[pts[:, 0], pts[:, 1]].astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(u0))
+
+
+def test_full_size_eigenmode_fp32():
+    """A Dirichlet sine mode on the 8192^2 grid decays by lam^T exactly."""
+    sg = sgmod()
+    p = c2_2d5p()
+    ny, nx = p.shape
+    ky, kx = 3, 5
+    phi = np.multiply.outer(sine_mode_1d(ny, ky), sine_mode_1d(nx, kx))
+    w = f32_weights(p.weights)
+    lam = w[0] + (w[1] + w[2]) * np.cos(np.pi * ky / (ny + 1)) + (w[3] + w[4]) * np.cos(np.pi * kx / (nx + 1))
+    plan = sg.stencil_plan_create(2, 1, p.shape, STAR, p.weights, DIRICHLET, 0.0, sg.STENCIL_F32)
+    got = gpu_run(plan, phi.astype(np.float32), p.T).cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - lam ** p.T * phi)) <= 2e-5
+
+
+# ------------------------------------------------------------- API edges
+def test_run_host_matches_device_run():
+    sg = sgmod()
+    shape, T = (77, 131), 9
+    w = box_weights(2, 1, 1 / 9)
+    plan = sg.stencil_plan_create(2, 1, shape, BOX, w, PERIODIC, 0.0, sg.STENCIL_F32)
+    u0 = uniform01(3, shape[0] * shape[1]).reshape(shape).astype(np.float32)
+    dev = gpu_run(plan, u0, T).cpu().numpy()
+    h_in = torch.from_numpy(u0).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    sg.stencil_run_host(plan, h_in, h_out, T)
+    np.testing.assert_array_equal(h_out.numpy(), dev)
+
+
+def test_zero_steps_and_ragged_pass_counts():
+    sg = sgmod()
+    shape = (40, 64)
+    w = star_weights(2, 1, 0.5, 0.125)
+    plan = sg.stencil_plan_create(2, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+    u0 = uniform01(4, shape[0] * shape[1]).reshape(shape).astype(np.float32)
+    np.testing.assert_array_equal(gpu_run(plan, u0, 0).cpu().numpy(), u0)
+    base = gpu_run(plan, u0, 11, variant=1).cpu().numpy()
+    for k in kvalues(plan):
+        np.testing.assert_array_equal(gpu_run(plan, u0, 11, k=k).cpu().numpy(), base)
+        assert sg.stencil_plan_launch_count(plan, 11) == -(-11 // k)
+
+
+def test_errors_are_reported():
+    sg = sgmod()
+    plan = sg.stencil_plan_create(2, 1, (16, 16), STAR, [1, 0, 0, 0, 0], DIRICHLET, 0.0, sg.STENCIL_F32)
+    x = torch.zeros((16, 16), device=DEV)
+    with pytest.raises(sg.StencilError) as e:
+        sg.stencil_run(plan, x, x, 3)
+    assert e.value.status == sg.STENCIL_ERR_INVALID_ARG
+    with pytest.raises(sg.StencilError) as e:
+        sg.stencil_plan_set_k(plan, 99)
+    assert e.value.status == sg.STENCIL_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+def test_reductions_against_oracle(dtype):
+    sg = sgmod()
+    n = 1_000_003
+    u = torch.from_numpy(uniform01(8, n) - 0.5).to(dtype).to(DEV)
+    t = torch.from_numpy(uniform01(9, n)).to(dtype).to(DEV)
+    uh = u.double().cpu().numpy()
+    th = t.double().cpu().numpy()
+    bound = n * 2.0 ** -52
+    got = sg.stencil_reduce(u, sg.STENCIL_REDUCE_SUM).item()
+    assert abs(got - oracle.total(uh)) <= bound * np.sum(np.abs(uh))
+    got = sg.stencil_reduce(u, sg.STENCIL_REDUCE_SUMSQ).item()
+    assert abs(got - oracle.sumsq(uh)) <= bound * np.sum(uh * uh)
+    got = sg.stencil_reduce(u, sg.STENCIL_REDUCE_HALF_SQDIST, target=t).item()
+    exp = 0.5 * oracle.sumsq(uh - th)
+    assert abs(got - exp) <= bound * exp
+    again = sg.stencil_reduce(u, sg.STENCIL_REDUCE_HALF_SQDIST, target=t).item()
+    assert again == got      # fixed order: deterministic
