@@ -19,7 +19,7 @@ SG_DECL_F2(I32)
 #undef SG_DECL_F2
 
 int fused2d_max_k(const stencil_plan_s &P) {
-    if (P.dim != 2 || P.r > 2) return 0;
+    if (P.dim != 2 || P.r > 2 || P.n[1] > (1ll << 30)) return 0;
     switch (P.dtype) {
         case STENCIL_F32: return f2_kmax_F32(P.r);
         case STENCIL_F64: return f2_kmax_F64(P.r);
@@ -51,6 +51,37 @@ std::string fused2d_describe(const stencil_plan_s &P, int k) {
         case STENCIL_I32: bw = f2_bw_I32(P.r, k); break;
     }
     return "fused2d(warp-streamed rows, k=" + std::to_string(k) + ", band=" + std::to_string(bw) + " cols)";
+}
+
+#define SG_DECL_F3(DT) cudaError_t launch_f3_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+SG_DECL_F3(F32)
+SG_DECL_F3(F64)
+SG_DECL_F3(BF16)
+SG_DECL_F3(F16)
+SG_DECL_F3(I32)
+#undef SG_DECL_F3
+
+// 3D: r <= 2; k <= 4 (r = 1) or 2 (r = 2), bounded by the partial planes
+// each lane keeps in registers and by the window's y-halo.
+int fused3d_max_k(const stencil_plan_s &P) {
+    if (P.dim != 3 || P.r > 2 || P.n[0] > (1ll << 30) || P.n[1] > (1ll << 30)) return 0;
+    if (P.r == 2) return P.pattern == STENCIL_BOX ? 1 : 2;   // the r = 2 box spills beyond k = 1
+    return 4;
+}
+
+cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    switch (P.dtype) {
+        case STENCIL_F32: return launch_f3_F32(P, src, dst, k, st);
+        case STENCIL_F64: return launch_f3_F64(P, src, dst, k, st);
+        case STENCIL_BF16: return launch_f3_BF16(P, src, dst, k, st);
+        case STENCIL_F16: return launch_f3_F16(P, src, dst, k, st);
+        case STENCIL_I32: return launch_f3_I32(P, src, dst, k, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+std::string fused3d_describe(const stencil_plan_s &P, int k) {
+    return "fused3d(z-streamed planes, 16 warps x 2 rows, k=" + std::to_string(k) + ")";
 }
 
 int fused_max_k(const stencil_plan_s &P) {

@@ -157,7 +157,7 @@ __device__ __forceinline__ void load_row_reg(const typename Traits<DT>::S *__res
 // ------------------------------------------------------------- one job
 // Advances the rows [yo0, yo1) x columns [xo0, xo0 + BW) of one grid by K
 // steps.  Returns false if a bounded wait gave up (caller records status).
-template <int DT, int R, int PAT, int K, int PROD, bool COH>
+template <int DT, int R, int PAT, int K, int PROD, bool COH, bool MASK>
 __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typename Traits<DT>::S *__restrict__ src,
                                             typename Traits<DT>::S *__restrict__ dst, int64_t nx, int64_t ny,
                                             bool dir, typename Traits<DT>::C bval, const typename Traits<DT>::C *wr,
@@ -168,18 +168,25 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     using G = F2Geo<DT, R, K>;
     using Sh = Shape<2, R, PAT>;
     constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, NS = 2 * R;
+    // step unroll: the partial-row slots repeat every 2R rows; the register
+    // prefetch ring (PROD_REG) every F2_PREF rows
+    constexpr int U = PROD == PROD_TMA ? NS : F2_U;
+    static_assert(F2_ROWS % U == 0 && F2_U % NS == 0, "unroll");
     constexpr uint32_t FULLM = (1u << V) - 1u;
 
+    // row indices fit in 32 bits (checked by the launcher)
     const int64_t xw0 = xo0 - H;
     const int64_t xl = xw0 + (int64_t)lane * V;
-    const int64_t yi0 = yo0 - (int64_t)R * K;
-    const int nsteps = (int)(yo1 - yo0) + 2 * R * K;
-    const int nsp = round_up_c(nsteps, F2_U);
+    const int ny32 = (int)ny;
+    const int yi0 = (int)yo0 - R * K;
+    const int yo0i = (int)yo0, yo1i = (int)yo1;
+    const int nsteps = (yo1i - yo0i) + 2 * R * K;
+    const int nsp = round_up_c(nsteps, U);
     uint32_t cmask = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v)
         if (xl + v >= 0 && xl + v < nx) cmask |= 1u << v;
-    const bool need_cmask = dir && __any_sync(0xffffffffu, cmask != FULLM);
+    const bool need_cmask = MASK && __any_sync(0xffffffffu, cmask != FULLM);
     const bool lane_out = (lane * V >= H) && (lane * V < H + BW);
 
     int nst = 0;
@@ -210,11 +217,11 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
             for (int v = 0; v < V; ++v) P[s][m][v] = C(0);
 
-    for (int i0 = 0; i0 < nsp; i0 += F2_U) {
+    for (int i0 = 0; i0 < nsp; i0 += U) {
 #pragma unroll
-        for (int ph = 0; ph < F2_U; ++ph) {
+        for (int ph = 0; ph < U; ++ph) {
             const int i = i0 + ph;
-            const int64_t yin = yi0 + i;
+            const int yin = yi0 + i;
             C cur[V];
             int q = 0, rr = 0;
             if constexpr (PROD == PROD_TMA) {
@@ -238,10 +245,10 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) cur[v] = ring[ph % F2_PREF][v];
-                load_row_reg<DT, COH>(src, nx, ny, !dir, bval, yin + F2_PREF, xl, vec_ok, ring[ph % F2_PREF]);
+                load_row_reg<DT, COH>(src, nx, ny, !dir, bval, (int64_t)yin + F2_PREF, xl, vec_ok, ring[ph % F2_PREF]);
             }
-            if (dir) {
-                if (yin < 0 || yin >= ny) {
+            if constexpr (MASK) {
+                if ((unsigned)yin >= (unsigned)ny32) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) cur[v] = bval;
                 } else if (need_cmask) {
@@ -301,9 +308,9 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                     }
                 }
                 // emitted row Y = yin - (s+1)R: Dirichlet cells keep the boundary value
-                if (dir) {
-                    const int64_t ye = yin - (int64_t)(s + 1) * R;
-                    if (ye < 0 || ye >= ny) {
+                if constexpr (MASK) {
+                    const int ye = yin - (s + 1) * R;
+                    if ((unsigned)ye >= (unsigned)ny32) {
 #pragma unroll
                         for (int v = 0; v < V; ++v) emit[v] = bval;
                     } else if (need_cmask) {
@@ -316,9 +323,9 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                 for (int v = 0; v < V; ++v) cur[v] = emit[v];
             }
             // level-K row
-            const int64_t yout = yin - (int64_t)K * R;
-            if (yout >= yo0 && yout < yo1 && lane_out) {
-                S *rowp = dst + yout * nx;
+            const int yout = yin - K * R;
+            if (yout >= yo0i && yout < yo1i && lane_out) {
+                S *rowp = dst + (int64_t)yout * nx;
                 if (vec_ok && xl + V <= nx) {
                     stvec<DT>(rowp + xl, cur);
                 } else {
@@ -374,9 +381,18 @@ __global__ void __launch_bounds__(F2_NW * 32)
         const int64_t band = job % p.bands, chunk = job / p.bands;
         const int64_t yo0 = chunk * p.Ly;
         const int64_t yo1 = yo0 + p.Ly < p.g.n1 ? yo0 + p.Ly : p.g.n1;
-        const bool ok = fused2d_job<DT, R, PAT, K, PROD, false>(
-            &tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), p.g.n2, p.g.n1, dir, p.g.bval, wr,
-            band * G::BW, yo0, yo1, p.vec_ok != 0, stg, bars, gst, lane);
+        const int64_t xo0 = band * G::BW;
+        // jobs whose window and rows lie inside the domain never see a
+        // Dirichlet cell: they run without any masking code
+        const bool interior = !dir || (xo0 - G::H >= 0 && xo0 - G::H + G::W <= p.g.n2 && yo0 - R * K >= 0 &&
+                                       yo1 + R * K <= p.g.n1);
+        const bool ok = interior
+            ? fused2d_job<DT, R, PAT, K, PROD, false, false>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+                                                            p.g.n2, p.g.n1, dir, p.g.bval, wr, xo0, yo0, yo1,
+                                                            p.vec_ok != 0, stg, bars, gst, lane)
+            : fused2d_job<DT, R, PAT, K, PROD, false, true>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+                                                           p.g.n2, p.g.n1, dir, p.g.bval, wr, xo0, yo0, yo1,
+                                                           p.vec_ok != 0, stg, bars, gst, lane);
         if (!ok) {
             if (lane == 0) record_status(p.status, kStatusTimeout);
             return;
@@ -406,6 +422,7 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.status = P.d_status;
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1];
+    if (ny + 4 * R * K + 64 >= (1ll << 31)) return cudaErrorNotSupported;   // rows are 32-bit in the kernel
     p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
     bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && ((uintptr_t)src % 16 == 0) &&
                nx < (1ll << 31) && ny < (1ll << 31);

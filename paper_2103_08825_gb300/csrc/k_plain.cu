@@ -49,85 +49,103 @@ __device__ __forceinline__ void st4(S *p, const C in[4]) {
     }
 }
 
-template <int DT, int D, int R, int PAT>
-__global__ void __launch_bounds__(256) plain_kernel(const PlainParams<typename Traits<DT>::C> p) {
+// One 4-point group of row (i0, i1) starting at x0.  INNER: the whole
+// neighbourhood lies inside the grid, so no boundary logic runs.
+template <int DT, int D, int R, int PAT, bool INNER>
+__device__ __forceinline__ void plain_group(const PlainParams<typename Traits<DT>::C> &p,
+                                            const typename Traits<DT>::S *__restrict__ src,
+                                            typename Traits<DT>::S *__restrict__ dst, int64_t i0, int64_t i1,
+                                            int64_t x0) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
     using Sh = Shape<D, R, PAT>;
     constexpr int VX = 4;
-    const S *__restrict__ src = static_cast<const S *>(p.src);
-    S *__restrict__ dst = static_cast<S *>(p.dst);
     const int64_t n0 = p.g.n0, n1 = p.g.n1, n2 = p.g.n2;
     const bool periodic = p.g.bkind == STENCIL_PERIODIC;
     const C bval = p.g.bval;
-    const int64_t groups = (n2 + VX - 1) / VX;
-    const int64_t total = n0 * n1 * groups;
-
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = t % groups, row = t / groups;
-        const int64_t i1 = row % n1, i0 = row / n1;
-        const int64_t x0 = g * VX;
-        const bool x_inner = (x0 - R >= 0) && (x0 + VX + R <= n2);
-        C acc[VX];
-        bool first = true;
+    const S *centre = src + (i0 * n1 + i1) * n2;
+    C acc[VX];
+    bool first = true;
 #pragma unroll
-        for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz) {
+    for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz) {
 #pragma unroll
-            for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy) {
-                if (!Sh::inc(oz, oy, 0) && !(PAT == STENCIL_BOX)) continue;
-                const bool halo = (PAT == STENCIL_BOX) || (oz == 0 && oy == 0);
+        for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy) {
+            if (!Sh::inc(oz, oy, 0)) continue;
+            const bool halo = (PAT == STENCIL_BOX) || (oz == 0 && oy == 0);
+            C span[VX + 2 * R];
+            if constexpr (INNER) {
+                const S *rowp = centre + ((int64_t)oz * n1 + oy) * n2;
+                if (p.vec_ok) {
+                    ldg4<S, C>(rowp + x0, span + R);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VX; ++q) span[R + q] = to_c(__ldg(rowp + x0 + q));
+                }
+                if (halo) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        span[q] = to_c(__ldg(rowp + x0 - R + q));
+                        span[R + VX + q] = to_c(__ldg(rowp + x0 + VX + q));
+                    }
+                }
+            } else {
                 int64_t r0 = i0 + oz, r1 = i1 + oy;
                 bool row_ok = true;
                 if (r0 < 0 || r0 >= n0) { if (periodic) r0 = wrap_idx(r0, n0); else row_ok = false; }
                 if (r1 < 0 || r1 >= n1) { if (periodic) r1 = wrap_idx(r1, n1); else row_ok = false; }
                 const S *rowp = src + (r0 * n1 + r1) * n2;
-                C span[VX + 2 * R];
-                if (!row_ok) {
 #pragma unroll
-                    for (int q = 0; q < VX + 2 * R; ++q) span[q] = bval;
-                } else if (x_inner) {
-                    if (p.vec_ok) {
-                        ldg4<S, C>(rowp + x0, span + R);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < VX; ++q) span[R + q] = to_c(__ldg(rowp + x0 + q));
-                    }
-                    if (halo) {
-#pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            span[q] = to_c(__ldg(rowp + x0 - R + q));
-                            span[R + VX + q] = to_c(__ldg(rowp + x0 + VX + q));
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < VX + 2 * R; ++q) {
-                        if (!halo && (q < R || q >= R + VX)) continue;
-                        int64_t x = x0 - R + q;
-                        if (x >= 0 && x < n2) span[q] = to_c(__ldg(rowp + x));
-                        else if (periodic) span[q] = to_c(__ldg(rowp + wrap_idx(x, n2)));
-                        else span[q] = bval;
-                    }
-                }
-#pragma unroll
-                for (int ox = -R; ox <= R; ++ox) {
-                    if (!Sh::inc(oz, oy, ox)) continue;
-                    const C w = p.w[Sh::widx(oz, oy, ox)];
-#pragma unroll
-                    for (int v = 0; v < VX; ++v)
-                        acc[v] = first ? op_mul(w, span[R + v + ox]) : op_fma(w, span[R + v + ox], acc[v]);
-                    first = false;
+                for (int q = 0; q < VX + 2 * R; ++q) {
+                    if (!halo && (q < R || q >= R + VX)) continue;
+                    const int64_t x = x0 - R + q;
+                    if (!row_ok) span[q] = bval;
+                    else if (x >= 0 && x < n2) span[q] = to_c(__ldg(rowp + x));
+                    else if (periodic) span[q] = to_c(__ldg(rowp + wrap_idx(x, n2)));
+                    else span[q] = bval;
                 }
             }
-        }
-        S *out = dst + (i0 * n1 + i1) * n2;
-        if (p.vec_ok && x0 + VX <= n2) {
-            st4<S, C>(out + x0, acc);
-        } else {
 #pragma unroll
-            for (int v = 0; v < VX; ++v)
-                if (x0 + v < n2) out[x0 + v] = from_c<S>(acc[v]);
+            for (int ox = -R; ox <= R; ++ox) {
+                if (!Sh::inc(oz, oy, ox)) continue;
+                const C w = p.w[Sh::widx(oz, oy, ox)];
+#pragma unroll
+                for (int v = 0; v < VX; ++v)
+                    acc[v] = first ? op_mul(w, span[R + v + ox]) : op_fma(w, span[R + v + ox], acc[v]);
+                first = false;
+            }
+        }
+    }
+    S *out = dst + (i0 * n1 + i1) * n2;
+    if (p.vec_ok && x0 + VX <= n2) {
+        st4<S, C>(out + x0, acc);
+    } else {
+#pragma unroll
+        for (int v = 0; v < VX; ++v)
+            if (x0 + v < n2) out[x0 + v] = from_c<S>(acc[v]);
+    }
+}
+
+template <int DT, int D, int R, int PAT>
+__global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ PlainParams<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    constexpr int VX = 4;
+    const S *__restrict__ src = static_cast<const S *>(p.src);
+    S *__restrict__ dst = static_cast<S *>(p.dst);
+    const int64_t n0 = p.g.n0, n1 = p.g.n1, n2 = p.g.n2;
+    const int64_t groups = (n2 + VX - 1) / VX;
+    // grid: x over 4-point groups of a row, y over rows, z over planes
+    for (int64_t i0 = blockIdx.z; i0 < n0; i0 += gridDim.z) {
+        const bool z_in = D < 3 || (i0 >= R && i0 + R < n0);
+        for (int64_t i1 = blockIdx.y; i1 < n1; i1 += gridDim.y) {
+            const bool zy_in = z_in && (D < 2 || (i1 >= R && i1 + R < n1));
+            for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+                 g += (int64_t)gridDim.x * blockDim.x) {
+                const int64_t x0 = g * VX;
+                if (zy_in && x0 - R >= 0 && x0 + VX + R <= n2)
+                    plain_group<DT, D, R, PAT, true>(p, src, dst, i0, i1, x0);
+                else
+                    plain_group<DT, D, R, PAT, false>(p, src, dst, i0, i1, x0);
+            }
         }
     }
 }
@@ -161,11 +179,12 @@ static cudaError_t launch_plain_t(const stencil_plan_s &P, const void *src, void
     p.np = P.np;
     p.vec_ok = (P.n[2] % 4 == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_weight<C>(P.w_eval[j]);
-    const int64_t total = P.n[0] * P.n[1] * ((P.n[2] + 3) / 4);
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > (int64_t)P.sm_count * 64) blocks = (int64_t)P.sm_count * 64;
-    if (blocks < 1) blocks = 1;
-    plain_kernel<DT, D, R, PAT><<<(unsigned)blocks, 256, 0, st>>>(p);
+    const int64_t groups = (P.n[2] + 3) / 4;
+    int64_t bx = (groups + 255) / 256;
+    if (bx > (1ll << 30)) bx = 1ll << 30;
+    const dim3 grid((unsigned)bx, (unsigned)(P.n[1] < 65535 ? P.n[1] : 65535),
+                    (unsigned)(P.n[0] < 65535 ? P.n[0] : 65535));
+    plain_kernel<DT, D, R, PAT><<<grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -250,3 +250,119 @@ def test_reductions_against_oracle(dtype):
     assert abs(got - exp) <= bound * exp
     again = sg.stencil_reduce(u, sg.STENCIL_REDUCE_HALF_SQDIST, target=t).item()
     assert again == got      # fixed order: deterministic
+
+
+# ------------------------------------------------------------------- 3D
+SHAPES_3D = [(37, 53, 260), (9, 10, 36), (20, 70, 131)]
+
+
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_3d_int32_and_fp32_every_k(pattern, bkind):
+    """3D fused kernel (TMA and cp.async paths, several tiles in x, y and z):
+    int32 bit-exact against the oracle, FP32 bit-identical to the plain
+    sweep and within 1e-5 of the FP64 oracle."""
+    sg = sgmod()
+    rng = np.random.default_rng(77 + pattern + 2 * bkind)
+    for shape in SHAPES_3D:
+        n = int(np.prod(shape))
+        w = [float(x) for x in rng.integers(-2, 5, npoints(3, 1, pattern))]
+        bval = 31 if bkind == DIRICHLET else 0
+        u0 = uniform_u16(1300, n).reshape(shape)
+        plan = sg.stencil_plan_create(3, 1, shape, pattern, w, bkind, bval, sg.STENCIL_I32)
+        T = 9
+        ref = oracle.run_int(3, 1, pattern, shape, w, bkind, bval, u0, T)
+        for k in kvalues(plan):
+            np.testing.assert_array_equal(gpu_run(plan, u0, T, k=k).cpu().numpy(), ref, err_msg=f"{shape} k={k}")
+        wf = list(rng.uniform(0.0, 1.0, npoints(3, 1, pattern)))
+        wf = [x / sum(wf) for x in wf]
+        uf = uniform01(1301, n).reshape(shape).astype(np.float32)
+        pf = sg.stencil_plan_create(3, 1, shape, pattern, wf, bkind, 0.2 if bkind == DIRICHLET else 0.0,
+                                    sg.STENCIL_F32)
+        reff = oracle.run(3, 1, pattern, shape, f32_weights(wf), bkind, float(np.float32(0.2)) if bkind == DIRICHLET
+                          else 0.0, uf.astype(np.float64), T)
+        base = gpu_run(pf, uf, T, variant=1).cpu().numpy()
+        assert normwise(base, reff) <= 1e-5
+        for k in kvalues(pf):
+            np.testing.assert_array_equal(gpu_run(pf, uf, T, k=k).cpu().numpy(), base, err_msg=f"{shape} k={k}")
+
+
+@pytest.mark.parametrize("r,pattern", [(2, STAR), (2, BOX)])
+def test_3d_radius2(r, pattern):
+    sg = sgmod()
+    shape, T = (15, 22, 68), 5
+    rng = np.random.default_rng(5)
+    w = [float(x) for x in rng.integers(-2, 5, npoints(3, r, pattern))]
+    u0 = uniform_u16(1400, int(np.prod(shape))).reshape(shape)
+    for bkind in (DIRICHLET, PERIODIC):
+        plan = sg.stencil_plan_create(3, r, shape, pattern, w, bkind, 4 if bkind == DIRICHLET else 0, sg.STENCIL_I32)
+        ref = oracle.run_int(3, r, pattern, shape, w, bkind, 4 if bkind == DIRICHLET else 0, u0, T)
+        for k in kvalues(plan):
+            np.testing.assert_array_equal(gpu_run(plan, u0, T, k=k).cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dt,ur", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11), ("f64", 0.0)])
+def test_3d_other_dtypes(dt, ur):
+    sg = sgmod()
+    code = {"bf16": sg.STENCIL_BF16, "f16": sg.STENCIL_F16, "f64": sg.STENCIL_F64}[dt]
+    shape, T = (33, 40, 136), 12
+    w = star_weights(3, 1, 0.4, 0.1)
+    plan = sg.stencil_plan_create(3, 1, shape, STAR, w, DIRICHLET, 0.0, code)
+    u0 = uniform01(1500, int(np.prod(shape))).reshape(shape)
+    if dt == "f64":
+        ref = oracle.run(3, 1, STAR, shape, w, DIRICHLET, 0.0, u0, T)
+        base = gpu_run(plan, u0, T, variant=1).cpu().numpy()
+        assert normwise(base, ref) <= 1e-12
+        for k in kvalues(plan):
+            np.testing.assert_array_equal(gpu_run(plan, u0, T, k=k).cpu().numpy(), base)
+        return
+    u32 = u0.astype(np.float32)
+    uq = torch.from_numpy(u32).to(sg.torch_dtype(code)).float().numpy().astype(np.float64)
+    ref = oracle.run(3, 1, STAR, shape, f32_weights(w), DIRICHLET, 0.0, uq, T)
+    for k in kvalues(plan):
+        got = gpu_run(plan, u32, T, k=k).float().cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - ref)) <= (-(-T // k) * ur + 1e-5) * np.max(np.abs(uq)), k
+
+
+def sample_points_3d(shape, n_random=40, seed=7):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    pts = {(0, 0, 0), (nz - 1, ny - 1, nx - 1), (0, ny - 1, 0), (nz // 2, 0, nx - 1)}
+    for x in (119, 120, 239, 240, 111, 112):   # x seams of the fused 3D tiles
+        pts.add((int(rng.integers(0, nz)), int(rng.integers(0, ny)), x))
+    for y in (23, 24, 25, 27, 28, 29, 30, 31):   # y seams
+        pts.add((int(rng.integers(0, nz)), y, int(rng.integers(0, nx))))
+    for _ in range(n_random):
+        pts.add(tuple(int(rng.integers(0, s)) for s in shape))
+    return np.array(sorted(pts), dtype=np.int64)
+
+
+@pytest.mark.parametrize("maker", ["c3_3d7p", "c3_3d27p"])
+def test_full_size_3d_sampled(maker):
+    """512^3, T=32, FP32 and BF16 storage at the plan's default k: sampled
+    outputs against the oracle's dependency cones; FP32 bit-identical to the
+    plain sweep over the whole grid."""
+    import synth
+    sg = sgmod()
+    p = getattr(synth, maker)()
+    u0 = synth.u0_modes_plus_noise(p, np.float32)
+    plan = sg.stencil_plan_create(3, 1, p.shape, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_F32)
+    fused = gpu_run(plan, u0, p.T)
+    plain = gpu_run(plan, u0, p.T, variant=1)
+    assert torch.equal(fused, plain)
+    del plain
+    pts = sample_points_3d(p.shape)
+    ref = oracle.points(3, 1, p.pattern, p.shape, f32_weights(p.weights), p.bkind, p.bval,
+                        u0.astype(np.float64), p.T, pts)
+    got = fused.cpu().numpy()[pts[:, 0], pts[:, 1], pts[:, 2]].astype(np.float64)
+    scale = np.max(np.abs(u0))
+    assert np.max(np.abs(got - ref)) <= 1e-5 * scale
+    del fused
+    pb = sg.stencil_plan_create(3, 1, p.shape, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_BF16)
+    k = sg.stencil_plan_get_k(pb)
+    xb = torch.from_numpy(u0).to(torch.bfloat16)
+    uq = xb.float().numpy().astype(np.float64)
+    refq = oracle.points(3, 1, p.pattern, p.shape, f32_weights(p.weights), p.bkind, p.bval, uq, p.T, pts)
+    gotb = gpu_run(pb, u0, p.T)
+    gb = gotb.float().cpu().numpy()[pts[:, 0], pts[:, 1], pts[:, 2]].astype(np.float64)
+    assert np.max(np.abs(gb - refq)) <= (-(-p.T // k) * 2.0 ** -8 + 1e-5) * np.max(np.abs(uq))
