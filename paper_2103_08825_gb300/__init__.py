@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "stencil_reduce": (st, [i32, i64, vp, vp, i32, vp, vp]),
         "stencil_get_device_status": (st, [vp]),
         "stencil_status_string": (ctypes.c_char_p, [st]),
+        "stencil_batch_test_skip_publish": (st, [vp, i64]),
         "stencil_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -246,3 +247,59 @@ def stencil_status_string(status: int) -> str:
 
 def stencil_last_error() -> str:
     return load().stencil_last_error().decode()
+
+
+class Batch:
+    """Owns a stencil_batch_t (destroyed with the object)."""
+
+    def __init__(self, handle, shapes, dtype):
+        self.handle, self.shapes, self.dtype = handle, [tuple(s) for s in shapes], dtype
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.stencil_batch_destroy(h)
+            self.handle = None
+
+
+def stencil_batch_create(shapes, weights, T, pattern: int, radius: int = 1, bkind: int = STENCIL_PERIODIC,
+                         bval: float = 0.0, dtype: int = STENCIL_F32) -> Batch:
+    """A batch of 2D grids (shapes: list of (ny, nx); weights: list of compact
+    weight lists; T: list of step counts)."""
+    lib = load()
+    n = len(shapes)
+    sh = (ctypes.c_int64 * (2 * n))(*[int(v) for s in shapes for v in s])
+    keep = [(ctypes.c_double * len(w))(*[float(x) for x in w]) for w in weights]
+    ws = (stencil_weights_t * n)(*[stencil_weights_t(pattern, len(w), k) for w, k in zip(weights, keep)])
+    ts = (ctypes.c_int64 * n)(*[int(t) for t in T])
+    b = stencil_boundary_t(bkind, float(bval))
+    h = ctypes.c_void_p()
+    _check(lib.stencil_batch_create(ctypes.byref(h), n, 2, radius, sh, ws, ts, ctypes.byref(b), dtype),
+           "stencil_batch_create")
+    return Batch(h, shapes, dtype)
+
+
+def stencil_batch_run(batch: Batch, u_in, u_out, stream=None):
+    """u_out[i] := T[i] steps applied to u_in[i] (lists of CUDA tensors)."""
+    n = len(batch.shapes)
+    if len(u_in) != n or len(u_out) != n:
+        raise ValueError("one input and one output tensor per batch member")
+    for i, (a, b) in enumerate(zip(u_in, u_out)):
+        for t, nm in ((a, "u_in"), (b, "u_out")):
+            if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != batch.shapes[i] or \
+                    _dtype_code(t.dtype) != batch.dtype:
+                raise ValueError(f"{nm}[{i}] must be a contiguous CUDA tensor of shape {batch.shapes[i]}")
+    pin = (ctypes.c_void_p * n)(*[t.data_ptr() for t in u_in])
+    pout = (ctypes.c_void_p * n)(*[t.data_ptr() for t in u_out])
+    _check(load().stencil_batch_run(batch.handle, pin, pout, _stream_handle(stream)), "stencil_batch_run")
+    return u_out
+
+
+def stencil_batch_get_device_status(batch: Batch) -> int:
+    return int(load().stencil_batch_get_device_status(batch.handle))
+
+
+def stencil_batch_launch_count(batch: Batch) -> int:
+    n = ctypes.c_int64()
+    _check(load().stencil_batch_launch_count(batch.handle, ctypes.byref(n)), "stencil_batch_launch_count")
+    return n.value

@@ -1,0 +1,482 @@
+// k_batch.cu -- many independent 2D grids advanced by one persistent kernel.
+//
+// Not in the paper (which runs one grid at a time): grids of uneven size and
+// step count share the GPU through a work queue.  Each grid's passes (k
+// fused steps, the last one T mod k) are cut into warp-sized tiles (one
+// column band x Ly rows).  Items (grid, pass, tile) are listed pass-major;
+// worker warps take the next item from an atomic ticket, wait until the
+// item's neighbouring tiles (3 x 3, wrapped for periodic grids) have finished
+// the previous pass -- the only tiles whose outputs its input window reads
+// and whose inputs its output overwrites -- then run the same warp-streamed
+// fused job as stencil_run and publish completion.  Because every
+// dependency precedes the item in the queue and all workers are resident,
+// the waits always end; they are still bounded (about one second of
+// wall time), and one that gives up raises an abort flag that stops every
+// worker and sets the batch's status word to STENCIL_ERR_TIMEOUT.
+//
+// The kernel plus the counter resets are captured into a CUDA graph on the
+// first stencil_batch_run and replayed afterwards.
+#include <string.h>
+
+#include <cmath>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "k_fused2d.cuh"
+#include "plan.h"
+
+namespace sg {
+
+constexpr int BT_NW = 4;          // warps per CTA
+constexpr int BT_LY = 64;         // output rows per tile
+constexpr int BT_MAXW = 25;
+
+template <typename C> struct BatchGrid {
+    const void *in;
+    void *out;
+    void *ws;
+    int ny, nx;
+    int passes, k_last;
+    int bands, chunks;
+    int tile_base;       // index of this grid's first tile counter
+    int pad;
+    C w[BT_MAXW];        // evaluation order
+};
+
+struct BatchCtl {
+    unsigned long long ticket;
+    int abort;
+    int status;
+};
+
+template <typename C> struct BatchParams {
+    const BatchGrid<C> *grids;
+    const unsigned long long *items;   // grid | pass << 16 | tile << 32
+    long long nitems;
+    int *done;                         // passes finished, per tile
+    BatchCtl *ctl;
+    int bkind;
+    C bval;
+    int *test_skip_publish;            // test hook: never publish this item (host-side fault injection)
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until counter >= target, the abort flag rises, or ~1 s passes.
+__device__ __forceinline__ bool wait_counter(const int *ctr, int target, const int *abort_flag) {
+    if (ld_acquire(ctr) >= target) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_relaxed(abort_flag)) return false;
+        if (global_ns() - t0 > 1000000000ull) return false;
+        __nanosleep(it < 16 ? 32 : 256);
+    }
+    return false;
+}
+
+template <int DT, int R, int PAT, int K, int KB, bool MASK>
+__device__ __forceinline__ void batch_job(const BatchGrid<typename Traits<DT>::C> &G, const void *src, void *dst,
+                                          bool dir, typename Traits<DT>::C bval,
+                                          const typename Traits<DT>::C *wr, int64_t xo0, int64_t yo0, int64_t yo1,
+                                          bool vec_ok, uint32_t &gst, int lane) {
+    using S = typename Traits<DT>::S;
+    // tiles are cut with k = KB's band width; a shorter last pass must write
+    // exactly the same columns
+    static_assert(F2Geo<DT, R, K>::BW == F2Geo<DT, R, KB>::BW, "band width must not depend on k <= KB");
+    fused2d_job<DT, R, PAT, K, PROD_REG, true, MASK>(nullptr, static_cast<const S *>(src), static_cast<S *>(dst),
+                                                     G.nx, G.ny, dir, bval, wr, xo0, yo0, yo1, vec_ok, nullptr,
+                                                     nullptr, gst, lane);
+}
+
+template <int DT, int R, int PAT, int KB>
+__global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant__ BatchParams<typename Traits<DT>::C> p) {
+    using C = typename Traits<DT>::C;
+    using Sh = Shape<2, R, PAT>;
+    const int lane = threadIdx.x & 31;
+    const bool dir = p.bkind == STENCIL_DIRICHLET;
+    uint32_t gst = 0;
+    while (true) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(&p.ctl->ticket, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((long long)q >= p.nitems) break;
+        if (__shfl_sync(0xffffffffu, lane == 0 ? ld_relaxed(&p.ctl->abort) : 0, 0)) break;
+        const unsigned long long item = p.items[q];
+        const int g = (int)(item & 0xffffull), pass = (int)((item >> 16) & 0xffffull), t = (int)(item >> 32);
+        const BatchGrid<C> &G = p.grids[g];
+        const int b = t % G.bands, c = t / G.bands;
+        // dependencies: the 3 x 3 neighbourhood of the tile, previous pass
+        bool ok = true;
+        if (pass > 0 && lane < 9) {
+            int nb = b + lane % 3 - 1, nc = c + lane / 3 - 1;
+            bool skip = false;
+            if (nb < 0 || nb >= G.bands) { if (dir) skip = true; else nb = (nb + G.bands) % G.bands; }
+            if (nc < 0 || nc >= G.chunks) { if (dir) skip = true; else nc = (nc + G.chunks) % G.chunks; }
+            if (!skip) ok = wait_counter(&p.done[G.tile_base + nc * G.bands + nb], pass, &p.ctl->abort);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicExch(&p.ctl->abort, 1);
+                atomicCAS(&p.ctl->status, 0, kStatusTimeout);
+            }
+            break;
+        }
+        __threadfence();
+        // buffers: the last pass writes `out`, earlier ones alternate ws / out
+        const void *src = pass == 0 ? G.in : (((G.passes - pass) % 2 == 0) ? G.out : G.ws);
+        void *dst = ((G.passes - 1 - pass) % 2 == 0) ? G.out : G.ws;
+        const int kp = pass == G.passes - 1 ? G.k_last : KB;
+        C wr[Sh::npts];
+#pragma unroll
+        for (int j = 0; j < Sh::npts; ++j) wr[j] = G.w[j];
+        using Geo = F2Geo<DT, R, KB>;
+        const int64_t xo0 = (int64_t)b * Geo::BW;
+        const int64_t yo0 = (int64_t)c * BT_LY;
+        const int64_t yo1 = yo0 + BT_LY < G.ny ? yo0 + BT_LY : G.ny;
+        const bool vec_ok = (G.nx % Traits<DT>::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+        // tiles are laid out with the band width of k = KB; shorter last
+        // passes use the same tiles (their halo is smaller)
+        const bool interior = !dir || (xo0 - Geo::H >= 0 && xo0 - Geo::H + Geo::W <= G.nx && yo0 - R * KB >= 0 &&
+                                       yo1 + R * KB <= G.ny);
+#define SG_BJ(KK)                                                                                           \
+    if (interior) batch_job<DT, R, PAT, KK, KB, false>(G, src, dst, dir, p.bval, wr, xo0, yo0, yo1, vec_ok, gst, lane); \
+    else batch_job<DT, R, PAT, KK, KB, true>(G, src, dst, dir, p.bval, wr, xo0, yo0, yo1, vec_ok, gst, lane);
+        switch (kp) {
+            case 1: { SG_BJ(1) break; }
+            case 2: { if constexpr (KB >= 2) { SG_BJ(2) } break; }
+            case 3: { if constexpr (KB >= 3) { SG_BJ(3) } break; }
+            case 4: { if constexpr (KB >= 4) { SG_BJ(4) } break; }
+        }
+#undef SG_BJ
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            if (!(p.test_skip_publish && *p.test_skip_publish == (int)q)) atomicAdd(&p.done[G.tile_base + t], 1);
+        }
+    }
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+struct stencil_batch_s {
+    int n = 0, r = 0, pattern = 0, dtype = 0, bkind = 0, kb = 4;
+    double bval = 0.0;
+    int device = 0, sm_count = 0;
+    std::vector<int64_t> ny, nx, T;
+    std::vector<size_t> bytes;
+    void *d_grids = nullptr;          // BatchGrid<C>[n]
+    std::vector<unsigned char> h_grids;
+    size_t grid_desc_size = 0;
+    unsigned long long *d_items = nullptr;
+    long long nitems = 0;
+    int *d_done = nullptr;
+    long long ntiles = 0;
+    BatchCtl *d_ctl = nullptr;
+    int *d_skip = nullptr;            // test hook (fault injection), null unless enabled
+    std::vector<void *> ws;
+    std::vector<const void *> last_in;
+    std::vector<void *> last_out;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid_ctas = 0;
+};
+
+namespace {
+
+int tile_bw(int dtype, int r, int kb) {
+    // band width of the 2D fused job for (dtype, r, k = kb)
+    const int v = dtype == STENCIL_F64 ? 2 : 4;
+    const int al = std::max(16 / (int)dtype_size(dtype), v);
+    const int h = (r * kb + al - 1) / al * al;
+    return 32 * v - 2 * h;
+}
+
+template <int DT>
+stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weights) {
+    using C = typename Traits<DT>::C;
+    const int n = B->n;
+    B->grid_desc_size = sizeof(BatchGrid<C>);
+    B->h_grids.assign(sizeof(BatchGrid<C>) * n, 0);
+    BatchGrid<C> *hg = reinterpret_cast<BatchGrid<C> *>(B->h_grids.data());
+    const int bw = tile_bw(DT, B->r, B->kb);
+    // evaluation (lexicographic) order of the compact 2D weights
+    const int np = B->pattern == STENCIL_BOX ? (2 * B->r + 1) * (2 * B->r + 1) : 1 + 4 * B->r;
+    std::vector<std::pair<int, int>> offs(np);
+    if (B->pattern == STENCIL_BOX) {
+        for (int j = 0; j < np; ++j) offs[j] = {j / (2 * B->r + 1) - B->r, j % (2 * B->r + 1) - B->r};
+    } else {
+        int j = 1;
+        offs[0] = {0, 0};
+        for (int m = -B->r; m <= B->r; ++m) if (m) offs[j++] = {m, 0};
+        for (int m = -B->r; m <= B->r; ++m) if (m) offs[j++] = {0, m};
+    }
+    std::vector<int> order(np);
+    for (int j = 0; j < np; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return offs[a] < offs[b]; });
+    long long tiles = 0;
+    int maxp = 0;
+    std::vector<int> passes(n);
+    for (int g = 0; g < n; ++g) {
+        BatchGrid<C> &G = hg[g];
+        G.ny = (int)B->ny[g];
+        G.nx = (int)B->nx[g];
+        const int64_t T = B->T[g];
+        G.passes = (int)((T + B->kb - 1) / B->kb);
+        G.k_last = (int)(T - (int64_t)(G.passes - 1) * B->kb);
+        G.bands = (G.nx + bw - 1) / bw;
+        G.chunks = (G.ny + BT_LY - 1) / BT_LY;
+        G.tile_base = (int)tiles;
+        tiles += (long long)G.bands * G.chunks;
+        for (int j = 0; j < np; ++j) G.w[j] = conv_w<C>(weights[g].w[order[j]]);
+        passes[g] = G.passes;
+        maxp = std::max(maxp, G.passes);
+    }
+    B->ntiles = tiles;
+    std::vector<unsigned long long> items;
+    for (int p = 0; p < maxp; ++p)
+        for (int g = 0; g < n; ++g)
+            if (p < passes[g])
+                for (int t = 0; t < hg[g].bands * hg[g].chunks; ++t)
+                    items.push_back((unsigned long long)g | ((unsigned long long)p << 16) |
+                                    ((unsigned long long)t << 32));
+    B->nitems = (long long)items.size();
+    cudaError_t e = cudaMalloc(&B->d_grids, B->h_grids.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(unsigned long long) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_done, sizeof(int) * std::max<long long>(1, tiles));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_ctl, sizeof(BatchCtl));
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("batch allocation failed"); return STENCIL_ERR_OOM; }
+    if (!items.empty())
+        e = cudaMemcpy(B->d_items, items.data(), sizeof(unsigned long long) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_error("batch upload failed"); return STENCIL_ERR_CUDA; }
+    B->ws.assign(n, nullptr);
+    for (int g = 0; g < n; ++g) {
+        if (passes[g] < 2) continue;   // a single pass reads `in` and writes `out` only
+        e = cudaMalloc(&B->ws[g], B->bytes[g]);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("batch workspace allocation failed"); return STENCIL_ERR_OOM; }
+    }
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<DT, 1, STENCIL_BOX, 4>, BT_NW * 32, 0);
+    B->grid_ctas = B->sm_count * std::max(1, bps);
+    return STENCIL_OK;
+}
+
+template <int DT>
+cudaError_t launch_batch(stencil_batch_s *B, cudaStream_t st) {
+    using C = typename Traits<DT>::C;
+    BatchParams<C> p;
+    p.grids = static_cast<const BatchGrid<C> *>(B->d_grids);
+    p.items = B->d_items;
+    p.nitems = B->nitems;
+    p.done = B->d_done;
+    p.ctl = B->d_ctl;
+    p.bkind = B->bkind;
+    p.bval = conv_w<C>(B->bval);
+    p.test_skip_publish = B->d_skip;
+    const bool box = B->pattern == STENCIL_BOX;
+    // the resident-worker bound keeps every dequeued item's dependencies running
+    int bps = 0;
+    auto kern = B->r == 1 ? (box ? batch_kernel<DT, 1, STENCIL_BOX, 4> : batch_kernel<DT, 1, STENCIL_STAR, 4>)
+                          : (box ? batch_kernel<DT, 2, STENCIL_BOX, 2> : batch_kernel<DT, 2, STENCIL_STAR, 2>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BT_NW * 32, 0);
+    const int ctas = B->sm_count * std::max(1, bps);
+    kern<<<ctas, BT_NW * 32, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch(stencil_batch_s *B, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B->d_done, 0, sizeof(int) * std::max<long long>(1, B->ntiles), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_ctl, 0, sizeof(BatchCtl), st);
+    if (e != cudaSuccess) return e;
+    switch (B->dtype) {
+        case STENCIL_F32: return launch_batch<STENCIL_F32>(B, st);
+        case STENCIL_I32: return launch_batch<STENCIL_I32>(B, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+extern "C" {
+
+stencil_status_t stencil_batch_create(stencil_batch_t *out, int32_t n, int32_t dim, int32_t radius,
+                                      const int64_t *shapes, const stencil_weights_t *weights, const int64_t *T,
+                                      const stencil_boundary_t *boundary, int32_t dtype) {
+    if (!out || !shapes || !weights || !T || !boundary || n < 1 || n > 65535) {
+        set_error("invalid batch arguments");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (dim != 2) { set_error("batches support dim = 2"); return STENCIL_ERR_UNSUPPORTED; }
+    if (radius < 1 || radius > 2) { set_error("batches support radius 1 or 2"); return STENCIL_ERR_UNSUPPORTED; }
+    if (dtype != STENCIL_F32 && dtype != STENCIL_I32) { set_error("batches support F32 and I32"); return STENCIL_ERR_UNSUPPORTED; }
+    if (boundary->kind != STENCIL_DIRICHLET && boundary->kind != STENCIL_PERIODIC) {
+        set_error("invalid boundary kind");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    const int pattern = weights[0].pattern;
+    if (pattern != STENCIL_STAR && pattern != STENCIL_BOX) { set_error("invalid pattern"); return STENCIL_ERR_INVALID_ARG; }
+    const int np = pattern == STENCIL_BOX ? (2 * radius + 1) * (2 * radius + 1) : 1 + 4 * radius;
+    stencil_batch_s *B = new (std::nothrow) stencil_batch_s();
+    if (!B) { set_error("host allocation failed"); return STENCIL_ERR_OOM; }
+    B->n = n; B->r = radius; B->pattern = pattern; B->dtype = dtype; B->bkind = boundary->kind;
+    B->bval = boundary->kind == STENCIL_DIRICHLET ? boundary->value : 0.0;
+    B->kb = radius == 1 ? 4 : 2;
+    for (int g = 0; g < n; ++g) {
+        const int64_t ny = shapes[2 * g], nx = shapes[2 * g + 1];
+        if (ny < 1 || nx < 1 || ny > (1 << 24) || nx > (1 << 24) || T[g] < 0 || T[g] > 65535 * (int64_t)B->kb ||
+            weights[g].pattern != pattern || weights[g].count != np || !weights[g].w) {
+            delete B;
+            set_error("invalid shape, step count or weights for batch member " + std::to_string(g));
+            return STENCIL_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < np; ++j) {
+            const double w = weights[g].w[j];
+            if (dtype == STENCIL_I32 && w != std::floor(w)) {
+                delete B;
+                set_error("integer mode needs integer weights");
+                return STENCIL_ERR_INVALID_ARG;
+            }
+        }
+        B->ny.push_back(ny);
+        B->nx.push_back(nx);
+        B->T.push_back(T[g]);
+        B->bytes.push_back((size_t)(ny * nx) * dtype_size(dtype));
+    }
+    cudaError_t e = cudaGetDevice(&B->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
+    if (e != cudaSuccess) { delete B; set_error("no CUDA device"); return STENCIL_ERR_CUDA; }
+    stencil_status_t s = dtype == STENCIL_F32 ? build_batch<STENCIL_F32>(B, weights) : build_batch<STENCIL_I32>(B, weights);
+    if (s != STENCIL_OK) { stencil_batch_destroy(B); return s; }
+    *out = B;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_destroy(stencil_batch_t B) {
+    if (!B) return STENCIL_OK;
+    cudaSetDevice(B->device);
+    cudaDeviceSynchronize();
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    cudaFree(B->d_grids);
+    cudaFree(B->d_items);
+    cudaFree(B->d_done);
+    cudaFree(B->d_ctl);
+    cudaFree(B->d_skip);
+    for (void *w : B->ws) cudaFree(w);
+    delete B;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_run(stencil_batch_t B, const void *const *u_in, void *const *u_out, void *stream) {
+    if (!B || !u_in || !u_out) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    // every output must be disjoint from every input and from the other outputs
+    struct Rng { const char *a; size_t n; int out; };
+    std::vector<Rng> rs;
+    for (int g = 0; g < B->n; ++g) {
+        if (!u_in[g] || !u_out[g]) { set_error("null grid pointer"); return STENCIL_ERR_INVALID_ARG; }
+        rs.push_back({static_cast<const char *>(u_in[g]), B->bytes[g], 0});
+        rs.push_back({static_cast<const char *>(u_out[g]), B->bytes[g], 1});
+    }
+    std::sort(rs.begin(), rs.end(), [](const Rng &x, const Rng &y) { return x.a < y.a; });
+    for (size_t i = 1; i < rs.size(); ++i)
+        if (rs[i].a < rs[i - 1].a + rs[i - 1].n && (rs[i].out || rs[i - 1].out)) {
+            set_error("batch outputs must not overlap inputs or other outputs");
+            return STENCIL_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // refresh the grid table when the caller's buffers change (stream-ordered,
+    // before the graph); pageable source, so the host copy is taken at once
+    bool changed = B->last_in.size() != (size_t)B->n;
+    for (int g = 0; !changed && g < B->n; ++g) changed = B->last_in[g] != u_in[g] || B->last_out[g] != u_out[g];
+    if (changed) {
+        const size_t ds = B->grid_desc_size;
+        for (int g = 0; g < B->n; ++g) {
+            unsigned char *d = B->h_grids.data() + ds * g;
+            const void *in = u_in[g];
+            void *outp = u_out[g];
+            memcpy(d, &in, sizeof(void *));
+            memcpy(d + sizeof(void *), &outp, sizeof(void *));
+            memcpy(d + 2 * sizeof(void *), &B->ws[g], sizeof(void *));
+        }
+        cudaError_t e = cudaMemcpyAsync(B->d_grids, B->h_grids.data(), B->h_grids.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { set_error(std::string("grid table upload: ") + cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+        B->last_in.assign(u_in, u_in + B->n);
+        B->last_out.assign(u_out, u_out + B->n);
+    }
+    if (!B->exec) {
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { set_error("stream creation failed"); return STENCIL_ERR_CUDA; }
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = enqueue_batch(B, cs);
+            e = cudaStreamEndCapture(cs, &B->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+            return STENCIL_ERR_CUDA;
+        }
+    }
+    for (int g = 0; g < B->n; ++g)   // members with T = 0 are copied
+        if (B->T[g] == 0) {
+            cudaError_t ce = cudaMemcpyAsync(u_out[g], u_in[g], B->bytes[g], cudaMemcpyDeviceToDevice, st);
+            if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); return STENCIL_ERR_CUDA; }
+        }
+    cudaError_t e = cudaGraphLaunch(B->exec, st);
+    if (e != cudaSuccess) { set_error(std::string("graph launch: ") + cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_get_device_status(stencil_batch_t B) {
+    if (!B) { set_error("null batch"); return STENCIL_ERR_INVALID_ARG; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+    BatchCtl h;
+    e = cudaMemcpy(&h, B->d_ctl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+    if (h.status) { set_error("a batch dependency wait gave up"); return (stencil_status_t)h.status; }
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_launch_count(stencil_batch_t B, int64_t *launches) {
+    if (!B || !launches) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    *launches = 1;
+    return STENCIL_OK;
+}
+
+// Test hook (not in the public header): makes item `q` skip its completion
+// publish, so that the items depending on it must give up their bounded
+// waits -- host-side fault injection for the timeout path.  q < 0 disables.
+stencil_status_t stencil_batch_test_skip_publish(stencil_batch_t B, int64_t q) {
+    if (!B) return STENCIL_ERR_INVALID_ARG;
+    if (!B->d_skip) {
+        if (cudaMalloc(&B->d_skip, sizeof(int)) != cudaSuccess) return STENCIL_ERR_OOM;
+    }
+    int v = (int)q;
+    if (cudaMemcpy(B->d_skip, &v, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return STENCIL_ERR_CUDA;
+    // the captured graph holds the old parameters: capture again
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    return STENCIL_OK;
+}
+
+}  // extern "C"

@@ -366,3 +366,51 @@ def test_full_size_3d_sampled(maker):
     gotb = gpu_run(pb, u0, p.T)
     gb = gotb.float().cpu().numpy()[pts[:, 0], pts[:, 1], pts[:, 2]].astype(np.float64)
     assert np.max(np.abs(gb - refq)) <= (-(-p.T // k) * 2.0 ** -8 + 1e-5) * np.max(np.abs(uq))
+
+
+# ------------------------------------------------------------------- 1D
+def test_1d3p_full_config_f64_and_int():
+    """The 1D workload at full size: 65536 points, T=100, FP64 (normwise
+    1e-12 against the oracle, every k bit-identical to the plain sweep) and
+    the int32 mode with weights 1/2/1 (bit-exact)."""
+    import synth
+    sg = sgmod()
+    p = synth.c1_1d3p()
+    u0 = synth.u0_uniform(p)
+    plan = sg.stencil_plan_create(1, 1, p.shape, STAR, p.weights, DIRICHLET, 0.0, sg.STENCIL_F64)
+    ref = oracle.run(1, 1, STAR, p.shape, p.weights, DIRICHLET, 0.0, u0, p.T)
+    base = gpu_run(plan, u0, p.T, variant=1).cpu().numpy()
+    assert normwise(base, ref) <= 1e-12
+    for k in kvalues(plan):
+        np.testing.assert_array_equal(gpu_run(plan, u0, p.T, k=k).cpu().numpy(), base, err_msg=f"k={k}")
+    pi = synth.c1_1d3p_int()
+    ui = synth.u0_int(pi)
+    plan_i = sg.stencil_plan_create(1, 1, pi.shape, STAR, pi.weights, DIRICHLET, 0.0, sg.STENCIL_I32)
+    refi = oracle.run_int(1, 1, STAR, pi.shape, pi.weights, DIRICHLET, 0, ui, pi.T)
+    for k in kvalues(plan_i):
+        np.testing.assert_array_equal(gpu_run(plan_i, ui, pi.T, k=k).cpu().numpy(), refi, err_msg=f"k={k}")
+
+
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+@pytest.mark.parametrize("n", [1, 5, 127, 128, 129, 4097, 100003])
+def test_1d_ragged_every_k(r, bkind, n):
+    sg = sgmod()
+    rng = np.random.default_rng(n + r + bkind)
+    w = [float(x) for x in rng.integers(-3, 6, 2 * r + 1)]
+    bval = 9 if bkind == DIRICHLET else 0
+    u0 = uniform_u16(1600 + n, n)
+    plan = sg.stencil_plan_create(1, r, (n,), STAR, w, bkind, bval, sg.STENCIL_I32)
+    T = 19
+    ref = oracle.run_int(1, r, STAR, (n,), w, bkind, bval, u0, T)
+    for k in kvalues(plan):
+        np.testing.assert_array_equal(gpu_run(plan, u0, T, k=k).cpu().numpy(), ref, err_msg=f"k={k}")
+    wf = [0.2, 0.5, 0.3] if r == 1 else [0.1, 0.2, 0.3, 0.25, 0.15]
+    uf = uniform01(1700 + n, n).astype(np.float32)
+    pf = sg.stencil_plan_create(1, r, (n,), STAR, wf, bkind, 0.25 if bkind == DIRICHLET else 0.0, sg.STENCIL_F32)
+    base = gpu_run(pf, uf, T, variant=1).cpu().numpy()
+    reff = oracle.run(1, r, STAR, (n,), f32_weights(wf), bkind, 0.25 if bkind == DIRICHLET else 0.0,
+                      uf.astype(np.float64), T)
+    assert normwise(base, reff) <= 1e-5
+    for k in kvalues(pf):
+        np.testing.assert_array_equal(gpu_run(pf, uf, T, k=k).cpu().numpy(), base, err_msg=f"k={k}")
