@@ -110,10 +110,13 @@ stencil_status_t stencil_plan_max_k(stencil_plan_t plan, int32_t *kmax);
 /* Select FUSED (default) or PLAIN kernels for stencil_run. */
 stencil_status_t stencil_plan_set_variant(stencil_plan_t plan, int32_t variant);
 
-/* Autotune the fusion depth: times stencil_run for every supported k on
- * plan-owned buffers holding zeros, with CUDA events on `stream`, and keeps
- * the fastest.  Synchronises `stream`.  `T` is the step count to tune for;
- * best_k / best_ms (may be NULL) receive the choice and its time. */
+/* Autotune the fusion depth: times stencil_run for the one-step kernel and
+ * for every supported k on plan-owned buffers holding zeros, with CUDA events
+ * on `stream`, and keeps the fastest (for tiny or FP64-pipe-bound grids the
+ * one-step kernel can win).  Synchronises `stream`.  `T` is the step count to
+ * tune for; best_k (may be NULL) receives the chosen k, or 0 when the
+ * one-step kernel won; best_ms (may be NULL) its time.  stencil_plan_set_k
+ * and stencil_plan_set_variant discard the choice. */
 stencil_status_t stencil_plan_tune(stencil_plan_t plan, int64_t T, void *stream, int32_t *best_k, double *best_ms);
 
 /* Number of kernel launches stencil_run makes for T steps with the current

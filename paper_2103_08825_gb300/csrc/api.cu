@@ -143,7 +143,7 @@ static int effective_k(const stencil_plan_s *P) {
 }
 
 static bool uses_fused(const stencil_plan_s *P) {
-    return P->variant == STENCIL_VARIANT_FUSED && fused_max_k(*P) > 0;
+    return P->variant == STENCIL_VARIANT_FUSED && !P->tuned_plain && fused_max_k(*P) > 0;
 }
 
 }  // namespace sg
@@ -268,6 +268,7 @@ stencil_status_t stencil_plan_set_k(stencil_plan_t P, int32_t k) {
         return STENCIL_ERR_UNSUPPORTED;
     }
     P->k = k;
+    P->tuned_plain = false;
     return STENCIL_OK;
 }
 
@@ -289,6 +290,7 @@ stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
         return STENCIL_ERR_INVALID_ARG;
     }
     P->variant = variant;
+    P->tuned_plain = false;
     return STENCIL_OK;
 }
 
@@ -379,8 +381,11 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     const int saved = P->k;
     int bk = 1;
     float bms = 1e30f;
-    for (int k = 1; k <= km; ++k) {
-        P->k = k;
+    bool best_plain = false;
+    // candidates: the one-step kernel (k = 0 here), then every fused depth
+    for (int k = 0; k <= km; ++k) {
+        P->tuned_plain = (k == 0);
+        P->k = k == 0 ? 1 : k;
         s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
         if (s != STENCIL_OK) break;
         float best_rep = 1e30f;
@@ -396,13 +401,14 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
             best_rep = std::min(best_rep, ms);
         }
         if (s != STENCIL_OK) break;
-        if (best_rep < bms) { bms = best_rep; bk = k; }
+        if (best_rep < bms) { bms = best_rep; bk = k == 0 ? 1 : k; best_plain = (k == 0); }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (s != STENCIL_OK) { P->k = saved; return s; }
+    if (s != STENCIL_OK) { P->k = saved; P->tuned_plain = false; return s; }
     P->k = bk;
-    if (best_k) *best_k = bk;
+    P->tuned_plain = best_plain;
+    if (best_k) *best_k = best_plain ? 0 : bk;
     if (best_ms) *best_ms = bms;
     return STENCIL_OK;
 }

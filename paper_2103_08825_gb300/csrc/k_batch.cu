@@ -4,10 +4,11 @@
 // step count share the GPU through a work queue.  Each grid's passes (k
 // fused steps, the last one T mod k) are cut into warp-sized tiles (one
 // column band x Ly rows).  Items (grid, pass, tile) are listed pass-major;
-// worker warps take the next item from an atomic ticket, wait until the
-// item's neighbouring tiles (3 x 3, wrapped for periodic grids) have finished
-// the previous pass -- the only tiles whose outputs its input window reads
-// and whose inputs its output overwrites -- then run the same warp-streamed
+// worker warps take the next item from an atomic ticket, wait until every
+// tile whose output meets the item's input window (wrapped for periodic
+// grids; listed on the host per column band and per row chunk) has finished
+// the previous pass -- exactly the tiles whose outputs it reads and whose
+// inputs its output overwrites -- then run the same warp-streamed
 // fused job as stencil_run and publish completion.  Because every
 // dependency precedes the item in the queue and all workers are resident,
 // the waits always end; they are still bounded (about one second of
@@ -42,7 +43,7 @@ template <typename C> struct BatchGrid {
     int passes, k_last;
     int bands, chunks;
     int tile_base;       // index of this grid's first tile counter
-    int pad;
+    int boff, coff;      // this grid's band / chunk offsets into dep_off
     C w[BT_MAXW];        // evaluation order
 };
 
@@ -57,6 +58,8 @@ template <typename C> struct BatchParams {
     const unsigned long long *items;   // grid | pass << 16 | tile << 32
     long long nitems;
     int *done;                         // passes finished, per tile
+    const int *dep_off;                // per band / chunk: range of its dependency list
+    const int *dep_list;               // bands (chunks) whose outputs meet its input window
     BatchCtl *ctl;
     int bkind;
     C bval;
@@ -119,14 +122,16 @@ __global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant
         const int g = (int)(item & 0xffffull), pass = (int)((item >> 16) & 0xffffull), t = (int)(item >> 32);
         const BatchGrid<C> &G = p.grids[g];
         const int b = t % G.bands, c = t / G.bands;
-        // dependencies: the 3 x 3 neighbourhood of the tile, previous pass
+        // dependencies: every tile of the previous pass whose output meets
+        // this tile's input window (= whose input window meets its output)
         bool ok = true;
-        if (pass > 0 && lane < 9) {
-            int nb = b + lane % 3 - 1, nc = c + lane / 3 - 1;
-            bool skip = false;
-            if (nb < 0 || nb >= G.bands) { if (dir) skip = true; else nb = (nb + G.bands) % G.bands; }
-            if (nc < 0 || nc >= G.chunks) { if (dir) skip = true; else nc = (nc + G.chunks) % G.chunks; }
-            if (!skip) ok = wait_counter(&p.done[G.tile_base + nc * G.bands + nb], pass, &p.ctl->abort);
+        if (pass > 0) {
+            const int b0 = p.dep_off[G.boff + b], nbx = p.dep_off[G.boff + b + 1] - b0;
+            const int c0 = p.dep_off[G.coff + c], ncy = p.dep_off[G.coff + c + 1] - c0;
+            for (int e = lane; e < nbx * ncy; e += 32) {
+                const int nb = p.dep_list[b0 + e % nbx], nc = p.dep_list[c0 + e / nbx];
+                ok = ok && wait_counter(&p.done[G.tile_base + nc * G.bands + nb], pass, &p.ctl->abort);
+            }
         }
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) {
@@ -184,6 +189,7 @@ struct stencil_batch_s {
     std::vector<unsigned char> h_grids;
     size_t grid_desc_size = 0;
     unsigned long long *d_items = nullptr;
+    int *d_dep_off = nullptr, *d_dep_list = nullptr;
     long long nitems = 0;
     int *d_done = nullptr;
     long long ntiles = 0;
@@ -248,6 +254,37 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
         maxp = std::max(maxp, G.passes);
     }
     B->ntiles = tiles;
+    // dependency lists per band (columns) and per chunk (rows): the tiles of
+    // the same grid whose output range meets the input window, wrapped for
+    // periodic grids and clipped for Dirichlet ones
+    const int hx = (32 * Traits<DT>::V - bw) / 2, hy = B->r * B->kb;
+    std::vector<int> dep_off, dep_list;
+    auto add_list = [&](int64_t lo, int64_t hi, int64_t n, int tile, int ntiles, bool periodic) {
+        std::vector<char> hit(ntiles, 0);
+        for (int64_t x = lo; x < hi; ++x) {
+            int64_t xx = x;
+            if (xx < 0 || xx >= n) {
+                if (!periodic) continue;
+                xx = ((xx % n) + n) % n;
+            }
+            hit[(int)(xx / tile < ntiles ? xx / tile : ntiles - 1)] = 1;
+        }
+        for (int t = 0; t < ntiles; ++t) if (hit[t]) dep_list.push_back(t);
+        dep_off.push_back((int)dep_list.size());
+    };
+    const bool per = B->bkind == STENCIL_PERIODIC;
+    for (int g = 0; g < n; ++g) {
+        BatchGrid<C> &G = hg[g];
+        G.boff = (int)dep_off.size();
+        dep_off.push_back((int)dep_list.size());
+        for (int b = 0; b < G.bands; ++b)
+            add_list((int64_t)b * bw - hx, std::min<int64_t>((int64_t)(b + 1) * bw, G.nx) + hx, G.nx, bw, G.bands, per);
+        G.coff = (int)dep_off.size();
+        dep_off.push_back((int)dep_list.size());
+        for (int c = 0; c < G.chunks; ++c)
+            add_list((int64_t)c * BT_LY - hy, std::min<int64_t>((int64_t)(c + 1) * BT_LY, G.ny) + hy, G.ny, BT_LY,
+                     G.chunks, per);
+    }
     std::vector<unsigned long long> items;
     for (int p = 0; p < maxp; ++p)
         for (int g = 0; g < n; ++g)
@@ -260,9 +297,15 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
     if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(unsigned long long) * std::max<size_t>(1, items.size()));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_done, sizeof(int) * std::max<long long>(1, tiles));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_ctl, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_dep_off, sizeof(int) * dep_off.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_dep_list, sizeof(int) * std::max<size_t>(1, dep_list.size()));
     if (e != cudaSuccess) { cudaGetLastError(); set_error("batch allocation failed"); return STENCIL_ERR_OOM; }
     if (!items.empty())
         e = cudaMemcpy(B->d_items, items.data(), sizeof(unsigned long long) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_dep_off, dep_off.data(), sizeof(int) * dep_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !dep_list.empty())
+        e = cudaMemcpy(B->d_dep_list, dep_list.data(), sizeof(int) * dep_list.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_error("batch upload failed"); return STENCIL_ERR_CUDA; }
     B->ws.assign(n, nullptr);
     for (int g = 0; g < n; ++g) {
@@ -284,6 +327,8 @@ cudaError_t launch_batch(stencil_batch_s *B, cudaStream_t st) {
     p.items = B->d_items;
     p.nitems = B->nitems;
     p.done = B->d_done;
+    p.dep_off = B->d_dep_off;
+    p.dep_list = B->d_dep_list;
     p.ctl = B->d_ctl;
     p.bkind = B->bkind;
     p.bval = conv_w<C>(B->bval);
@@ -378,6 +423,8 @@ stencil_status_t stencil_batch_destroy(stencil_batch_t B) {
     cudaFree(B->d_done);
     cudaFree(B->d_ctl);
     cudaFree(B->d_skip);
+    cudaFree(B->d_dep_off);
+    cudaFree(B->d_dep_list);
     for (void *w : B->ws) cudaFree(w);
     delete B;
     return STENCIL_OK;

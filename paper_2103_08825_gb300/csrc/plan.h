@@ -26,6 +26,7 @@ struct stencil_plan_s {
     int eval_to_compact[sg::kHostMaxPts] = {};
     int k = 0;                 // 0 = default
     int variant = STENCIL_VARIANT_FUSED;
+    bool tuned_plain = false;  // the tuner found the one-step kernel fastest
     int device = 0;
     int sm_count = 0;
     void *ws = nullptr;        // one grid: intermediate passes of stencil_run
