@@ -194,6 +194,28 @@ typedef enum {
 stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void *u, const void *target, int32_t op,
                                 double *out, void *stream);
 
+/* Allocation-free form of stencil_reduce, for callers that cannot allocate
+ * device memory when they reduce: devices or drivers without stream-ordered
+ * memory pools (stencil_reduce takes its partial-sum buffer with
+ * cudaMallocAsync), applications whose caching allocator already holds nearly
+ * all free device memory, and latency-critical loops that must not enter an
+ * allocator.  Same arguments, same summation order and so the same result as
+ * stencil_reduce, but the per-block partial sums live in a library-static
+ * device array of 1024 doubles (8 KiB), which every GPU that loads the
+ * library holds until the process exits; no cudaMalloc, cudaMallocAsync,
+ * cudaFree or other allocating call is made.  The reduction never uses more
+ * than 1024 partial sums, so n is not limited by the array; a call whose
+ * partition needed more would return STENCIL_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array
+ * (each call writes every partial it reads, so nothing needs clearing):
+ * calls whose kernels overlap on the GPU -- on different streams without
+ * ordering between them -- race and can return wrong sums.
+ * The paper has no counterpart to this entry point. */
+stencil_status_t stencil_reduce_noalloc(int32_t dtype, int64_t n, const void *u, const void *target, int32_t op,
+                                        double *out, void *stream);
+
 /* ------------------------------------------------------------------ status */
 
 /* Synchronises the plan's device and returns (then clears) its device

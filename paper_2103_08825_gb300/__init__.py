@@ -31,7 +31,8 @@ EXPORTS = [
     "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_tune", "stencil_plan_launch_count",
     "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_batch_create",
     "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status",
-    "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_reduce", "stencil_get_device_status",
+    "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_reduce", "stencil_reduce_noalloc",
+    "stencil_get_device_status",
     "stencil_status_string", "stencil_last_error",
 ]
 
@@ -86,6 +87,7 @@ def load(path: str | None = None):
         "stencil_batch_launch_count": (st, [vp, ctypes.POINTER(i64)]),
         "stencil_adjoint_run": (st, [vp, vp, vp, i64, i32, vp, vp, vp]),
         "stencil_reduce": (st, [i32, i64, vp, vp, i32, vp, vp]),
+        "stencil_reduce_noalloc": (st, [i32, i64, vp, vp, i32, vp, vp]),
         "stencil_get_device_status": (st, [vp]),
         "stencil_status_string": (ctypes.c_char_p, [st]),
         "stencil_batch_test_skip_publish": (st, [vp, i64]),
@@ -238,6 +240,20 @@ def stencil_reduce(u, op: int, target=None, out=None, stream=None):
     tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
     _check(load().stencil_reduce(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "stencil_reduce")
+    return out
+
+
+def stencil_reduce_noalloc(u, op: int, target=None, out=None, stream=None):
+    """stencil_reduce without any device allocation (partial sums in a
+    library-static array); `out` defaults to a new 1-element float64 tensor,
+    which the caller may preallocate to avoid torch's allocator as well."""
+    import torch
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+    tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
+    _check(load().stencil_reduce_noalloc(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "stencil_reduce_noalloc")
     return out
 
 

@@ -3,6 +3,7 @@
 // and summed in an order fixed by n alone (block b owns a contiguous range,
 // thread t a stride of it, then a fixed tree), so results do not depend on
 // the device or on timing.  Two passes: per-block partials, then one block.
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -126,6 +127,69 @@ extern "C" stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void 
     cudaError_t e2 = cudaFreeAsync(part, st);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         set_error(std::string("reduction launch: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return STENCIL_ERR_CUDA;
+    }
+    return STENCIL_OK;
+}
+
+// ------------------------------------------------------------------------
+// Allocation-free variant.  The partial sums of the first pass live in this
+// file-scope device array instead of a stream-ordered allocation.  Its size
+// is the largest number of partials the reduction ever uses (RED_MAX_BLOCKS
+// doubles, 8 KiB), and every GPU that loads the library keeps it until the
+// process exits.  Host code must not hand the array's host-side name to a
+// kernel: the device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+static __device__ __align__(256) double g_reduce_scratch[RED_MAX_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" stencil_status_t stencil_reduce_noalloc(int32_t dtype, int64_t n, const void *u, const void *target,
+                                                   int32_t op, double *out, void *stream) {
+    if (dtype == STENCIL_I32 || dtype < STENCIL_F64 || dtype > STENCIL_F16) {
+        set_error("stencil_reduce_noalloc supports F64, F32, BF16 and F16");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    if (n < 1 || !u || !out || op < STENCIL_REDUCE_SUM || op > STENCIL_REDUCE_HALF_SQDIST ||
+        (op == STENCIL_REDUCE_HALF_SQDIST && !target)) {
+        set_error("invalid reduction arguments");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    const int nb = reduce_blocks(n);
+    if (nb > RED_MAX_BLOCKS) {
+        set_error("stencil_reduce_noalloc: n needs " + std::to_string(nb) + " partial sums, more than the " +
+                  std::to_string(RED_MAX_BLOCKS) + " its static scratch holds");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_error("stencil_reduce_noalloc: no usable current device");
+        return STENCIL_ERR_CUDA;
+    }
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            // first call on this device: find the array's device address
+            e = cudaGetSymbolAddress(reinterpret_cast<void **>(&g_scratch_addr[dev]), g_reduce_scratch);
+            if (e != cudaSuccess) {
+                g_scratch_addr[dev] = nullptr;
+                set_error(std::string("stencil_reduce_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+                return STENCIL_ERR_CUDA;
+            }
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    // every partial slot the final pass reads is written by the first pass
+    // of the same call, so nothing needs clearing
+    e = reduce_launch(dtype, n, u, target, op, scratch, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_error(std::string("reduction launch: ") + cudaGetErrorString(e));
         return STENCIL_ERR_CUDA;
     }
     return STENCIL_OK;
