@@ -319,3 +319,58 @@ def stencil_batch_launch_count(batch: Batch) -> int:
     n = ctypes.c_int64()
     _check(load().stencil_batch_launch_count(batch.handle, ctypes.byref(n)), "stencil_batch_launch_count")
     return n.value
+
+
+def stencil_adjoint_run(plan: Plan, u0, grad_uT, T: int, ckpt_every: int, grad_u0=None, grad_w=None, stream=None):
+    """Reverse-mode derivative of T steps (FP32 plans): returns (grad_u0,
+    grad_w) for a loss whose gradient w.r.t. u_T is grad_uT."""
+    import torch
+    _check_grid(plan, u0, "u0")
+    _check_grid(plan, grad_uT, "grad_uT")
+    if grad_u0 is None:
+        grad_u0 = torch.empty_like(u0)
+    if grad_w is None:
+        grad_w = torch.empty(len(plan.weights), dtype=torch.float64, device=u0.device)
+    _check_grid(plan, grad_u0, "grad_u0")
+    _check(load().stencil_adjoint_run(plan.handle, ctypes.c_void_p(u0.data_ptr()), ctypes.c_void_p(grad_uT.data_ptr()),
+                                      int(T), int(ckpt_every), ctypes.c_void_p(grad_u0.data_ptr()),
+                                      ctypes.c_void_p(grad_w.data_ptr()), _stream_handle(stream)), "stencil_adjoint_run")
+    return grad_u0, grad_w
+
+
+def _autograd_fn():
+    import torch
+
+    class StencilFn(torch.autograd.Function):
+        """u_T = T stencil steps of u0 with the plan's weights.  Backward runs
+        stencil_adjoint_run: gradients w.r.t. u0 and the weights (compact
+        order; `weights` must hold the plan's coefficients)."""
+
+        @staticmethod
+        def forward(ctx, u0, weights, plan, T, ckpt_every=8):
+            u0 = u0.contiguous()
+            out = torch.empty_like(u0)
+            stencil_run(plan, u0, out, T)
+            ctx.save_for_backward(u0)
+            ctx.plan, ctx.T, ctx.ckpt = plan, int(T), int(min(max(1, ckpt_every), max(1, T)))
+            ctx.wdtype = weights.dtype
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (u0,) = ctx.saved_tensors
+            gu, gw = stencil_adjoint_run(ctx.plan, u0, grad_out.contiguous(), ctx.T, ctx.ckpt)
+            return gu, gw.to(ctx.wdtype), None, None, None
+
+    return StencilFn
+
+
+_stencil_fn = None
+
+
+def stencil_apply(u0, weights, plan: Plan, T: int, ckpt_every: int = 8):
+    """Differentiable T-step sweep (torch.autograd.Function over the C ABI)."""
+    global _stencil_fn
+    if _stencil_fn is None:
+        _stencil_fn = _autograd_fn()
+    return _stencil_fn.apply(u0, weights, plan, T, ckpt_every)

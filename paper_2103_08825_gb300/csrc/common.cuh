@@ -39,6 +39,18 @@ __device__ __forceinline__ double op_fma(double w, double u, double a) { return 
 __device__ __forceinline__ uint32_t op_mul(uint32_t w, uint32_t u) { return w * u; }
 __device__ __forceinline__ uint32_t op_fma(uint32_t w, uint32_t u, uint32_t a) { return w * u + a; }
 
+// Row updates acc[v] (+)= w * x[v], v < V, with op_mul / op_fma (scalar:
+// measured faster than the packed FP32x2 forms here, whose pair moves and
+// register pressure outweighed the halved FMA count).
+template <typename C, int V> __device__ __forceinline__ void row_fma_s(C w, const C *x, C *acc) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = op_fma(w, x[v], acc[v]);
+}
+template <typename C, int V> __device__ __forceinline__ void row_mul_s(C w, const C *x, C *acc) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = op_mul(w, x[v]);
+}
+
 // storage <-> arithmetic conversions (one rounding, to nearest even, on store)
 __device__ __forceinline__ float to_c(float v) { return v; }
 __device__ __forceinline__ double to_c(double v) { return v; }

@@ -1,0 +1,261 @@
+// k_adjoint.cu -- reverse-mode derivative of the T-step sweep (FP32 plans).
+//
+// Not in the paper.  The sweep is u_{t+1} = A u_t + c (c: the Dirichlet
+// boundary's constant contribution).  For a loss L(u_T) with lam_T = dL/du_T:
+//     dL/dw_j += sum_x lam_{t+1}[x] * u_t(x + o_j)      (boundary values included)
+//     lam_t    = A^T lam_{t+1},  (A^T lam)[y] = sum_j w_j lam[y - o_j]
+// for t = T-1 .. 0, and dL/du_0 = lam_0.  A^T is the stencil with reflected
+// offsets; lam outside a Dirichlet domain is 0 (boundary cells are constants),
+// periodic indices wrap.  One kernel does both lines of a backward step: it
+// reads lam_{t+1} and u_t once, writes lam_t, and adds its weight-gradient
+// terms (FP32 per thread over its four points, widened to FP64 for the block
+// sums) into per-block FP64 partials that persist across the steps; a final
+// one-block kernel sums the partials in a fixed order.
+//
+// Forward states are recomputed from checkpoints taken every `ckpt_every`
+// steps: the forward sweep (fused kernels) stores u_0, u_c, u_2c, ...; each
+// backward segment recomputes its c states with the one-step kernel, then
+// runs its c backward steps.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace sg {
+
+constexpr int ADJ_THREADS = 256;
+constexpr int ADJ_VX = 4;
+
+struct AdjParams {
+    const float *lam_in;   // lam_{t+1}
+    const float *u;        // u_t
+    float *lam_out;        // lam_t
+    double *partials;      // [gridDim.x][np]
+    int64_t n0, n1, n2;
+    int bkind;
+    float bval;
+    int first;             // 1: overwrite partials, 0: add
+    float w[kMaxPts];      // evaluation (lexicographic) order
+};
+
+template <int D, int R, int PAT>
+__global__ void __launch_bounds__(ADJ_THREADS) adjoint_step_kernel(const __grid_constant__ AdjParams p) {
+    using Sh = Shape<D, R, PAT>;
+    constexpr int NP = Sh::npts;
+    constexpr int NZ = D == 3 ? 2 * R + 1 : 1, NY = D >= 2 ? 2 * R + 1 : 1, SP = ADJ_VX + 2 * R;
+    __shared__ double red[ADJ_THREADS / 32][NP];
+    const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2;
+    const bool periodic = p.bkind == STENCIL_PERIODIC;
+    const int64_t groups = (n2 + ADJ_VX - 1) / ADJ_VX;
+    const int64_t rows = n0 * n1;
+    const int64_t items = rows * groups;
+    float gw[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) gw[j] = 0.f;
+    for (int64_t it = blockIdx.x * (int64_t)ADJ_THREADS + threadIdx.x; it < items;
+         it += (int64_t)gridDim.x * ADJ_THREADS) {
+        const int64_t g = it % groups, row = it / groups;
+        const int64_t i1 = row % n1, i0 = row / n1;
+        const int64_t x0 = g * ADJ_VX;
+        float lam[NZ][NY][SP], uu[NZ][NY][SP];
+#pragma unroll
+        for (int jz = 0; jz < NZ; ++jz)
+#pragma unroll
+            for (int jy = 0; jy < NY; ++jy) {
+                const int oz = D == 3 ? jz - R : 0, oy = D >= 2 ? jy - R : 0;
+                if (!Sh::inc(oz, oy, 0)) continue;
+                const bool halo = PAT == STENCIL_BOX || (oz == 0 && oy == 0);
+                int64_t z = i0 + oz, y = i1 + oy;
+                bool ok = true;
+                if (z < 0 || z >= n0) { if (periodic) z = wrap_idx(z, n0); else ok = false; }
+                if (y < 0 || y >= n1) { if (periodic) y = wrap_idx(y, n1); else ok = false; }
+                const int64_t base = (z * n1 + y) * n2;
+#pragma unroll
+                for (int q = 0; q < SP; ++q) {
+                    if (!halo && (q < R || q >= R + ADJ_VX)) continue;
+                    int64_t x = x0 - R + q;
+                    bool okx = ok;
+                    if (x < 0 || x >= n2) { if (periodic) x = wrap_idx(x, n2); else okx = false; }
+                    lam[jz][jy][q] = okx ? __ldg(p.lam_in + base + x) : 0.f;
+                    uu[jz][jy][q] = okx ? __ldg(p.u + base + x) : p.bval;
+                }
+            }
+        // lam_t[x] = sum_o w_o lam_{t+1}[x - o]; gw_o += lam_{t+1}[x] * u_t(x + o)
+        float acc[ADJ_VX];
+        bool first = true;
+#pragma unroll
+        for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz)
+#pragma unroll
+            for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy)
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    if (!Sh::inc(oz, oy, ox)) continue;
+                    const int j = Sh::widx(oz, oy, ox);
+                    const float w = p.w[j];
+                    const int rz = D == 3 ? R - oz : 0, ry = D >= 2 ? R - oy : 0;   // row of x - o
+                    const int fz = D == 3 ? R + oz : 0, fy = D >= 2 ? R + oy : 0;   // row of x + o
+#pragma unroll
+                    for (int v = 0; v < ADJ_VX; ++v) {
+                        const float l = lam[rz][ry][R + v - ox];
+                        acc[v] = first ? __fmul_rn(w, l) : __fmaf_rn(w, l, acc[v]);
+                        if (x0 + v < n2) gw[j] = __fmaf_rn(lam[D == 3 ? R : 0][D >= 2 ? R : 0][R + v], uu[fz][fy][R + v + ox], gw[j]);
+                    }
+                    first = false;
+                }
+        float *out = p.lam_out + (i0 * n1 + i1) * n2;
+#pragma unroll
+        for (int v = 0; v < ADJ_VX; ++v)
+            if (x0 + v < n2) out[x0 + v] = acc[v];
+    }
+    // block sums of the weight-gradient terms in FP64, fixed order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        double v = (double)gw[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double s = 0.0;
+        for (int wi = 0; wi < ADJ_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+        double *dst = p.partials + (size_t)blockIdx.x * NP + threadIdx.x;
+        *dst = p.first ? s : *dst + s;
+    }
+}
+
+// grad_w[compact j] = sum over blocks of partials[b][eval j], fixed order
+__global__ void adjoint_wgrad_final(const double *__restrict__ partials, int nblocks, int np,
+                                    const int *__restrict__ eval_to_compact, double *grad_w) {
+    __shared__ double sh[256];
+    for (int j = 0; j < np; ++j) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * np + j];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) grad_w[eval_to_compact[j]] = sh[0];
+        __syncthreads();
+    }
+}
+
+template <int D, int R, int PAT>
+static cudaError_t launch_adj_t(const AdjParams &p, int nblocks, cudaStream_t st) {
+    adjoint_step_kernel<D, R, PAT><<<nblocks, ADJ_THREADS, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_adj(const stencil_plan_s &P, const AdjParams &p, int nblocks, cudaStream_t st) {
+    const bool box = P.pattern == STENCIL_BOX;
+#define SG_ADJ(DD, RR)                                                                                  \
+    if (P.dim == DD && P.r == RR) return box ? launch_adj_t<DD, RR, STENCIL_BOX>(p, nblocks, st)        \
+                                             : launch_adj_t<DD, RR, STENCIL_STAR>(p, nblocks, st);
+    SG_ADJ(1, 1) SG_ADJ(1, 2) SG_ADJ(2, 1) SG_ADJ(2, 2) SG_ADJ(3, 1) SG_ADJ(3, 2)
+#undef SG_ADJ
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0, const void *grad_uT, int64_t T,
+                                                int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream) {
+    if (!P || !u0 || !grad_uT || !grad_u0 || !grad_w || T < 0) {
+        set_error("invalid argument");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (P->dtype != STENCIL_F32 || P->r > 2) {
+        set_error("the adjoint supports F32 plans of radius 1 or 2");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    if (T > 0 && (ckpt_every < 1 || ckpt_every > T)) {
+        set_error("ckpt_every must be in 1..T");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t gb = P->grid_bytes;
+    if (T == 0) {
+        cudaError_t e = cudaMemcpyAsync(grad_u0, grad_uT, gb, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grad_w, 0, sizeof(double) * P->np, st);
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+        return STENCIL_OK;
+    }
+    const int c = ckpt_every;
+    const int64_t M = (T + c - 1) / c;   // segments
+    // workspace: checkpoints 1..M-1, c-1 recomputed states, two lam grids
+    const size_t ngrids = (size_t)(M - 1) + (size_t)(c - 1) + 2;
+    const int64_t groups = (P->n[2] + ADJ_VX - 1) / ADJ_VX;
+    const int64_t items = P->n[0] * P->n[1] * groups;
+    int64_t nb = (items + ADJ_THREADS - 1) / ADJ_THREADS;
+    nb = std::min<int64_t>(nb, (int64_t)P->sm_count * 8);
+    const int nblocks = (int)std::max<int64_t>(1, nb);
+    const size_t need = ngrids * gb + 256 + sizeof(double) * (size_t)nblocks * P->np + sizeof(int) * P->np;
+    if (P->adj_ws_bytes < need) {
+        cudaFree(P->adj_ws);
+        P->adj_ws = nullptr;
+        P->adj_ws_bytes = 0;
+        if (cudaMalloc(&P->adj_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("adjoint workspace allocation of " + std::to_string(need) + " bytes failed");
+            return STENCIL_ERR_OOM;
+        }
+        P->adj_ws_bytes = need;
+    }
+    char *ws = static_cast<char *>(P->adj_ws);
+    auto grid_at = [&](size_t i) { return static_cast<void *>(ws + i * gb); };
+    double *partials = reinterpret_cast<double *>(ws + ((ngrids * gb + 255) / 256) * 256);
+    int *e2c = reinterpret_cast<int *>(partials + (size_t)nblocks * P->np);
+    std::vector<int> h_e2c(P->eval_to_compact, P->eval_to_compact + P->np);
+    cudaError_t e = cudaMemcpyAsync(e2c, h_e2c.data(), sizeof(int) * P->np, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+    // checkpoint m lives at grid m-1 (m >= 1); u0 is checkpoint 0
+    auto ckpt = [&](int64_t m) -> const void * { return m == 0 ? u0 : grid_at((size_t)(m - 1)); };
+    auto seg = [&](int i) -> void * { return grid_at((size_t)(M - 1) + (size_t)(i - 1)); };   // i = 1..c-1
+    void *lam[2] = {grid_at((size_t)(M - 1) + (size_t)(c - 1)), grid_at((size_t)(M - 1) + (size_t)c)};
+    // forward: checkpoints
+    for (int64_t m = 1; m < M; ++m) {
+        stencil_status_t s = stencil_run(P, ckpt(m - 1), grid_at((size_t)(m - 1)), c, stream);
+        if (s != STENCIL_OK) return s;
+    }
+    AdjParams p;
+    p.n0 = P->n[0];
+    p.n1 = P->n[1];
+    p.n2 = P->n[2];
+    p.bkind = P->bkind;
+    p.bval = (float)P->bval;
+    p.partials = partials;
+    for (int j = 0; j < P->np; ++j) p.w[j] = (float)P->w_eval[j];
+    const float *lam_next = static_cast<const float *>(grad_uT);
+    int li = 0;
+    bool first = true;
+    for (int64_t m = M - 1; m >= 0; --m) {
+        const int64_t t0 = m * c, t1 = std::min<int64_t>(T, t0 + c);
+        // recompute u_{t0+1} .. u_{t1-1} with one step per launch
+        for (int64_t t = t0 + 1; t < t1; ++t) {
+            const void *src = (t - 1 == t0) ? ckpt(m) : seg((int)(t - 1 - t0));
+            e = launch_plain(*P, src, seg((int)(t - t0)), st);
+            if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+        }
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            p.u = static_cast<const float *>(t == t0 ? ckpt(m) : seg((int)(t - t0)));
+            p.lam_in = lam_next;
+            p.lam_out = static_cast<float *>(t == 0 ? grad_u0 : lam[li]);
+            p.first = first ? 1 : 0;
+            e = launch_adj(*P, p, nblocks, st);
+            if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+            first = false;
+            lam_next = p.lam_out;
+            li ^= 1;
+        }
+    }
+    adjoint_wgrad_final<<<1, 256, 0, st>>>(partials, nblocks, P->np, e2c, grad_w);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+    return STENCIL_OK;
+}

@@ -15,8 +15,8 @@
 //             paper's Assemble, Section 3.2); the window's outer H >= rK
 //             columns are halo, recomputed redundantly (overlapped tiling);
 //   rows      a job covers Ly output rows and reads rK halo rows each side;
-//   input     PROD_TMA: lane 0 streams 8-row x W tiles by TMA
-//             (cp.async.bulk.tensor) into a 3-stage shared-memory ring per
+//   input     PROD_TMA: lane 0 streams 4-row x W tiles by TMA
+//             (cp.async.bulk.tensor) into a 4-stage shared-memory ring per
 //             warp, completion tracked by mbarriers (bounded waits; a timeout
 //             sets the status word).  Out-of-range rows/columns are
 //             zero-filled by TMA and then replaced by the Dirichlet value.
@@ -36,8 +36,8 @@
 namespace sg {
 
 constexpr int F2_NW = 4;       // warps per CTA (independent jobs)
-constexpr int F2_ROWS = 8;     // rows per TMA stage
-constexpr int F2_STAGES = 3;   // TMA ring depth per warp
+constexpr int F2_ROWS = 4;     // rows per TMA stage
+constexpr int F2_STAGES = 4;   // TMA ring depth per warp (3 stages = 12 rows in flight)
 constexpr int F2_PREF = 4;     // rows prefetched in registers (PROD_REG)
 constexpr int F2_U = 4;        // step unroll: multiple of 2R (R <= 2) and of F2_PREF
 enum { PROD_TMA = 0, PROD_REG = 1 };
@@ -187,6 +187,9 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     for (int v = 0; v < V; ++v)
         if (xl + v >= 0 && xl + v < nx) cmask |= 1u << v;
     const bool need_cmask = MASK && __any_sync(0xffffffffu, cmask != FULLM);
+    bool keep[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) keep[v] = (cmask >> v) & 1u;
     const bool lane_out = (lane * V >= H) && (lane * V < H + BW);
 
     int nst = 0;
@@ -217,31 +220,34 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
             for (int v = 0; v < V; ++v) P[s][m][v] = C(0);
 
+    // stage ring position: slot and phase parity advance once per stage
+    uint32_t slot = gst % F2_STAGES, par = (gst / F2_STAGES) & 1u;
+    int q = 0;                                   // stage index within the job
+    const S *srow = stg + slot * G::STAGE_ELEMS + lane * V;
     for (int i0 = 0; i0 < nsp; i0 += U) {
+        if constexpr (PROD == PROD_TMA) {
+            if ((i0 & (F2_ROWS - 1)) == 0) {
+                const bool ok = mbar_wait_bounded(&bars[slot], par);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    // give up: wait (bounded) for this warp's copies in flight
+                    if (lane == 0)
+                        for (int qq = q; qq < nst && qq < q + F2_STAGES; ++qq) {
+                            const uint32_t gg = gst + qq;
+                            mbar_wait_bounded(&bars[gg % F2_STAGES], (gg / F2_STAGES) & 1u);
+                        }
+                    __syncwarp();
+                    return false;
+                }
+                srow = stg + slot * G::STAGE_ELEMS + lane * V;
+            }
+        }
 #pragma unroll
         for (int ph = 0; ph < U; ++ph) {
             const int i = i0 + ph;
             const int yin = yi0 + i;
             C cur[V];
-            int q = 0, rr = 0;
             if constexpr (PROD == PROD_TMA) {
-                q = i / F2_ROWS;
-                rr = i - q * F2_ROWS;
-                const uint32_t g = gst + q, slot = g % F2_STAGES;
-                if (rr == 0) {
-                    const bool ok = mbar_wait_bounded(&bars[slot], (g / F2_STAGES) & 1u);
-                    if (__any_sync(0xffffffffu, !ok)) {
-                        // give up: wait (bounded) for this warp's copies in flight
-                        if (lane == 0)
-                            for (int qq = q; qq < nst && qq < q + F2_STAGES; ++qq) {
-                                const uint32_t gg = gst + qq;
-                                mbar_wait_bounded(&bars[gg % F2_STAGES], (gg / F2_STAGES) & 1u);
-                            }
-                        __syncwarp();
-                        return false;
-                    }
-                }
-                ldsvec<DT>(stg + slot * G::STAGE_ELEMS + rr * W + lane * V, cur);
+                ldsvec<DT>(srow + ((i0 & (F2_ROWS - 1)) + ph) * W, cur);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) cur[v] = ring[ph % F2_PREF][v];
@@ -253,8 +259,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                     for (int v = 0; v < V; ++v) cur[v] = bval;
                 } else if (need_cmask) {
 #pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if (!((cmask >> v) & 1u)) cur[v] = bval;
+                    for (int v = 0; v < V; ++v) cur[v] = keep[v] ? cur[v] : bval;
                 }
             }
 #pragma unroll
@@ -277,9 +282,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
                 for (int ox = -R; ox <= R; ++ox) {
                     if (!Sh::inc(0, R, ox)) continue;
-                    const C w = wr[Sh::widx(0, R, ox)];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) emit[v] = op_fma(w, ext[R + v + ox], emit[v]);
+                    row_fma_s<C, V>(wr[Sh::widx(0, R, ox)], &ext[R + ox], emit);
                 }
                 // rows Y = J - R + m (0 < m < 2R) take their o_y = R - m terms
 #pragma unroll
@@ -289,9 +292,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
                     for (int ox = -R; ox <= R; ++ox) {
                         if (!Sh::inc(0, oy, ox)) continue;
-                        const C w = wr[Sh::widx(0, oy, ox)];
-#pragma unroll
-                        for (int v = 0; v < V; ++v) P[s][sl][v] = op_fma(w, ext[R + v + ox], P[s][sl][v]);
+                        row_fma_s<C, V>(wr[Sh::widx(0, oy, ox)], &ext[R + ox], P[s][sl]);
                     }
                 }
                 // start Y = J + R with its o_y = -R terms (first term: multiply)
@@ -300,10 +301,8 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
                     for (int ox = -R; ox <= R; ++ox) {
                         if (!Sh::inc(0, -R, ox)) continue;
-                        const C w = wr[Sh::widx(0, -R, ox)];
-#pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            P[s][s0][v] = first ? op_mul(w, ext[R + v + ox]) : op_fma(w, ext[R + v + ox], P[s][s0][v]);
+                        if (first) row_mul_s<C, V>(wr[Sh::widx(0, -R, ox)], &ext[R + ox], P[s][s0]);
+                        else row_fma_s<C, V>(wr[Sh::widx(0, -R, ox)], &ext[R + ox], P[s][s0]);
                         first = false;
                     }
                 }
@@ -315,8 +314,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                         for (int v = 0; v < V; ++v) emit[v] = bval;
                     } else if (need_cmask) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            if (!((cmask >> v) & 1u)) emit[v] = bval;
+                        for (int v = 0; v < V; ++v) emit[v] = keep[v] ? emit[v] : bval;
                     }
                 }
 #pragma unroll
@@ -334,18 +332,19 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                         if (xl + v < nx) rowp[xl + v] = from_c<S>(cur[v]);
                 }
             }
-            if constexpr (PROD == PROD_TMA) {
-                if (rr == F2_ROWS - 1) {
-                    // stage consumed by every lane: refill it with the stage S ahead
-                    __syncwarp();
-                    if (lane == 0 && q + F2_STAGES < nst) {
-                        fence_proxy_async_smem();
-                        const uint32_t g = gst + q + F2_STAGES, slot = g % F2_STAGES;
-                        mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
-                        tma_load_2d(stg + slot * G::STAGE_ELEMS, tmap, &bars[slot], (int)xw0,
-                                    (int)(yi0 + (q + F2_STAGES) * F2_ROWS));
-                    }
+        }
+        if constexpr (PROD == PROD_TMA) {
+            if (((i0 + U) & (F2_ROWS - 1)) == 0) {
+                // stage consumed by every lane: refill it with the stage S ahead
+                __syncwarp();
+                if (lane == 0 && q + F2_STAGES < nst) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
+                    tma_load_2d(stg + slot * G::STAGE_ELEMS, tmap, &bars[slot], (int)xw0,
+                                yi0 + (q + F2_STAGES) * F2_ROWS);
                 }
+                ++q;
+                if (++slot == F2_STAGES) { slot = 0; par ^= 1u; }
             }
         }
     }
@@ -353,8 +352,11 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     return true;
 }
 
+// resident CTAs per SM the register allocation must allow, by fusion depth
+template <int K> constexpr int f2_min_blocks() { return K <= 3 ? 6 : K <= 5 ? 5 : K <= 6 ? 4 : 3; }
+
 template <int DT, int R, int PAT, int K, int PROD>
-__global__ void __launch_bounds__(F2_NW * 32)
+__global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     fused2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F2Params<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;

@@ -68,6 +68,19 @@ template <typename C> struct F3Params {
     C w[125];               // evaluation order; up to the r = 2 box
 };
 
+// V arithmetic values (16 or 32 bytes) to / from shared memory, 16-byte accesses
+template <typename C, int V> __device__ __forceinline__ void st_shared_vec(C *p, const C *v) {
+    static_assert((V * sizeof(C)) % 16 == 0, "16-byte units");
+#pragma unroll
+    for (int i = 0; i < (int)(V * sizeof(C)) / 16; ++i)
+        reinterpret_cast<uint4 *>(p)[i] = reinterpret_cast<const uint4 *>(v)[i];
+}
+template <typename C, int V> __device__ __forceinline__ void ld_shared_vec(const C *p, C *v) {
+#pragma unroll
+    for (int i = 0; i < (int)(V * sizeof(C)) / 16; ++i)
+        reinterpret_cast<uint4 *>(v)[i] = reinterpret_cast<const uint4 *>(p)[i];
+}
+
 __device__ __forceinline__ void cp_async4(void *smem, const void *g) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
 }
@@ -156,7 +169,11 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
     for (int v = 0; v < V; ++v)
         if (xl + v >= 0 && xl + v < nx) cmask |= 1u << v;
     const int row0 = warp * RY;                  // first own window row
-    const bool need_mask = MASK;
+    // columns outside the domain: only warps that hold some need the selects
+    bool keep[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) keep[v] = (cmask >> v) & 1u;
+    const bool need_cmask = MASK && __any_sync(0xffffffffu, cmask != FULLM);
     const bool lane_out = (lane * V >= H) && (lane * V < H + BW);
 
     // ---- prologue: first stages
@@ -219,20 +236,24 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     ldsvec<DT>(pl + wrow * W + lane * V, inc[j]);
                 }
                 if constexpr (MASK) {
-                    const bool zok = zin >= 0 && zin < nz;
+                    if (zin < 0 || zin >= nz) {                       // plane outside: uniform
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) {
-                        const int64_t y = yw0 + row0 - R + j;
-                        const bool rok = zok && y >= 0 && y < ny;
+                        for (int j = 0; j < NR; ++j)
 #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            if (!rok || !((cmask >> v) & 1u)) inc[j][v] = bval;
+                            for (int v = 0; v < V; ++v) inc[j][v] = bval;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NR; ++j) {
+                            const int64_t y = yw0 + row0 - R + j;     // warp-uniform
+                            if (y < 0 || y >= ny) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) inc[j][v] = bval;
+                            } else if (need_cmask) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) inc[j][v] = keep[v] ? inc[j][v] : bval;
+                            }
+                        }
                     }
-                } else if (false) {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j)
-#pragma unroll
-                        for (int v = 0; v < V; ++v) inc[j][v] = bval;
                 }
             }
             if constexpr (K == 1) __syncthreads();   // every warp has read the stage
@@ -268,10 +289,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                         if (!Sh::inc(R, oy, ox)) continue;
                         const C w = wr[Sh::widx(R, oy, ox)];
 #pragma unroll
-                        for (int j = 0; j < RY; ++j)
-#pragma unroll
-                            for (int v = 0; v < V; ++v)
-                                emit[j][v] = op_fma(w, ext[j + R + oy][R + v + ox], emit[j][v]);
+                        for (int j = 0; j < RY; ++j) row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], emit[j]);
                     }
                 // planes J - R + m take their o_z = R - m terms
 #pragma unroll
@@ -284,10 +302,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                             if (!Sh::inc(oz, oy, ox)) continue;
                             const C w = wr[Sh::widx(oz, oy, ox)];
 #pragma unroll
-                            for (int j = 0; j < RY; ++j)
-#pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                    P[s][sl][j][v] = op_fma(w, ext[j + R + oy][R + v + ox], P[s][sl][j][v]);
+                            for (int j = 0; j < RY; ++j) row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][sl][j]);
                         }
                 }
                 // start plane J + R: o_z = -R terms, first one a multiply
@@ -300,31 +315,32 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                             if (!Sh::inc(-R, oy, ox)) continue;
                             const C w = wr[Sh::widx(-R, oy, ox)];
 #pragma unroll
-                            for (int j = 0; j < RY; ++j)
-#pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                    P[s][s0][j][v] = first ? op_mul(w, ext[j + R + oy][R + v + ox])
-                                                           : op_fma(w, ext[j + R + oy][R + v + ox], P[s][s0][j][v]);
+                            for (int j = 0; j < RY; ++j) {
+                                if (first) row_mul_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][s0][j]);
+                                else row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][s0][j]);
+                            }
                             first = false;
                         }
                 }
                 // emitted plane index: Dirichlet cells keep the boundary value
                 const int64_t ze = zin - (int64_t)(s + 1) * R;
                 if constexpr (MASK) {
-                    const bool zok = ze >= 0 && ze < nz;
-                    if (!zok) {
+                    if (ze < 0 || ze >= nz) {                          // plane outside: uniform
 #pragma unroll
                         for (int j = 0; j < RY; ++j)
 #pragma unroll
                             for (int v = 0; v < V; ++v) emit[j][v] = bval;
-                    } else if (need_mask) {
+                    } else {
 #pragma unroll
                         for (int j = 0; j < RY; ++j) {
-                            const int64_t y = yw0 + row0 + j;
-                            const bool rok = y >= 0 && y < ny;
+                            const int64_t y = yw0 + row0 + j;          // warp-uniform
+                            if (y < 0 || y >= ny) {
 #pragma unroll
-                            for (int v = 0; v < V; ++v)
-                                if (!rok || !((cmask >> v) & 1u)) emit[j][v] = bval;
+                                for (int v = 0; v < V; ++v) emit[j][v] = bval;
+                            } else if (need_cmask) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) emit[j][v] = keep[v] ? emit[j][v] : bval;
+                            }
                         }
                     }
                 }
@@ -333,11 +349,8 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     C *xb = xbuf + (size_t)xpar * F3_NWY * G::XROWS * W;
 #pragma unroll
                     for (int qq = 0; qq < R; ++qq) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            xb[((size_t)warp * G::XROWS + qq) * W + lane * V + v] = emit[qq][v];
-                            xb[((size_t)warp * G::XROWS + R + qq) * W + lane * V + v] = emit[RY - R + qq][v];
-                        }
+                        st_shared_vec<C, V>(xb + ((size_t)warp * G::XROWS + qq) * W + lane * V, emit[qq]);
+                        st_shared_vec<C, V>(xb + ((size_t)warp * G::XROWS + R + qq) * W + lane * V, emit[RY - R + qq]);
                     }
                     __syncthreads();
                     if (s == 0 && PROD == PROD3_TMA && threadIdx.x == 0 && i + F3_STAGES < nsp) {
@@ -352,11 +365,8 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     const int wb = warp + 1 < F3_NWY ? warp + 1 : warp;
 #pragma unroll
                     for (int qq = 0; qq < R; ++qq) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            inc[qq][v] = xb[((size_t)wa * G::XROWS + R + qq) * W + lane * V + v];
-                            inc[R + RY + qq][v] = xb[((size_t)wb * G::XROWS + qq) * W + lane * V + v];
-                        }
+                        ld_shared_vec<C, V>(xb + ((size_t)wa * G::XROWS + R + qq) * W + lane * V, inc[qq]);
+                        ld_shared_vec<C, V>(xb + ((size_t)wb * G::XROWS + qq) * W + lane * V, inc[R + RY + qq]);
                     }
 #pragma unroll
                     for (int j = 0; j < RY; ++j)

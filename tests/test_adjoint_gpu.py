@@ -1,0 +1,130 @@
+"""The adjoint (transposed sweep backward in time with checkpoints) against
+the FP64 oracle adjoint, the dot-product identity and finite differences."""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import DIRICHLET, PERIODIC, STAR, BOX, c5_adjoint, f32_weights, npoints, uniform01
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def sgmod():
+    import paper_2103_08825_gb300 as sg
+    sg.load()
+    return sg
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b))))
+
+
+CASES = [
+    (3, 1, STAR, (32, 32, 32), PERIODIC, 0.0, 16, 8),
+    (3, 1, STAR, (20, 17, 24), DIRICHLET, 0.3, 9, 4),
+    (3, 1, BOX, (11, 13, 18), PERIODIC, 0.0, 7, 3),
+    (2, 1, BOX, (40, 37), DIRICHLET, -0.2, 12, 5),
+    (2, 2, STAR, (33, 30), PERIODIC, 0.0, 10, 10),
+    (1, 1, STAR, (301,), DIRICHLET, 0.5, 25, 6),
+    (1, 2, STAR, (77,), PERIODIC, 0.0, 8, 1),
+]
+
+
+@pytest.mark.parametrize("d,r,pattern,shape,bkind,bval,T,c", CASES)
+def test_adjoint_against_oracle(d, r, pattern, shape, bkind, bval, T, c):
+    sg = sgmod()
+    rng = np.random.default_rng(d * 10 + r + pattern + bkind)
+    w = list(rng.uniform(0.02, 0.3, npoints(d, r, pattern)))
+    n = int(np.prod(shape))
+    u0 = uniform01(5 + n, n).reshape(shape).astype(np.float32)
+    tg = uniform01(6 + n, n).reshape(shape).astype(np.float32)
+    plan = sg.stencil_plan_create(d, r, shape, pattern, w, bkind, bval, sg.STENCIL_F32)
+    x = torch.from_numpy(u0).to(DEV)
+    y = torch.empty_like(x)
+    sg.stencil_run(plan, x, y, T)
+    g = y - torch.from_numpy(tg).to(DEV)                  # dL/du_T of 0.5||u_T - target||^2
+    gu, gw = sg.stencil_adjoint_run(plan, x, g.contiguous(), T, c)
+    torch.cuda.synchronize()
+    loss, ogu, ogw = oracle.adjoint(d, r, pattern, shape, f32_weights(w), bkind, float(np.float32(bval)),
+                                    u0.astype(np.float64), tg.astype(np.float64), T)
+    assert rel(gu.cpu().numpy().astype(np.float64), ogu) <= 1e-4
+    assert rel(gw.cpu().numpy(), ogw) <= 1e-4
+
+
+def test_adjoint_dot_product_identity():
+    """<A^T y, x> = <y, A x> for one step (bval 0), on a periodic 3D grid."""
+    sg = sgmod()
+    shape = (24, 31, 40)
+    w = [0.4, 0.1, 0.1, 0.12, 0.08, 0.15, 0.05]
+    plan = sg.stencil_plan_create(3, 1, shape, STAR, w, PERIODIC, 0.0, sg.STENCIL_F32)
+    n = int(np.prod(shape))
+    x = torch.from_numpy(uniform01(1, n).reshape(shape).astype(np.float32) - 0.5).to(DEV)
+    yv = torch.from_numpy(uniform01(2, n).reshape(shape).astype(np.float32) - 0.5).to(DEV)
+    ax = torch.empty_like(x)
+    sg.stencil_run(plan, x, ax, 1)
+    aty, _ = sg.stencil_adjoint_run(plan, x, yv, 1, 1)
+    lhs = float((aty.double() * x.double()).sum())
+    rhs = float((yv.double() * ax.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * float((yv.double().abs() * ax.double().abs()).sum())
+
+
+def test_autograd_function_matches_adjoint():
+    sg = sgmod()
+    shape, T = (18, 21, 16), 6
+    w = [0.4, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1]
+    plan = sg.stencil_plan_create(3, 1, shape, STAR, w, PERIODIC, 0.0, sg.STENCIL_F32)
+    u0 = torch.rand(shape, device=DEV, requires_grad=True)
+    wt = torch.tensor(w, dtype=torch.float64, device=DEV, requires_grad=True)
+    out = sg.stencil_apply(u0, wt, plan, T, 2)
+    loss = 0.5 * (out.double() ** 2).sum()
+    loss.backward()
+    gu, gw = sg.stencil_adjoint_run(plan, u0.detach(), out.detach().contiguous(), T, 2)
+    assert torch.equal(u0.grad, gu)
+    assert torch.allclose(wt.grad, gw, rtol=1e-12, atol=0)
+
+
+def test_full_size_finite_differences():
+    """256^3 periodic 3D 7-point, T=64, checkpoints every 8: the u0 gradient
+    against central differences along two random directions (h = 1e-3; the
+    loss is quadratic in u0, so these are exact up to rounding) and the
+    weight gradient against central differences with h = 1e-5.  The loss is a
+    degree-2T polynomial in the weights whose mean mode grows like
+    (sum w)^64 over 16.7M points: its third derivative makes the O(h^2)
+    error of h = 1e-3 about ten times the gradient itself, while at h = 1e-5
+    it is ~0.1%; FP32 rounding noise in the FP64-reduced loss stays far
+    below both."""
+    sg = sgmod()
+    p = c5_adjoint()
+    n = p.npts
+    u0 = torch.from_numpy(uniform01(p.seed, n).reshape(p.shape).astype(np.float32)).to(DEV)
+    tg = torch.from_numpy(uniform01(p.extra["target_seed"], n).reshape(p.shape).astype(np.float32)).to(DEV)
+    y = torch.empty_like(u0)
+
+    def loss(wv, x):
+        pl = sg.stencil_plan_create(3, 1, p.shape, STAR, wv, PERIODIC, 0.0, sg.STENCIL_F32)
+        sg.stencil_run(pl, x, y, p.T)
+        return sg.stencil_reduce(y, sg.STENCIL_REDUCE_HALF_SQDIST, target=tg).item()
+
+    plan = sg.stencil_plan_create(3, 1, p.shape, STAR, p.weights, PERIODIC, 0.0, sg.STENCIL_F32)
+    sg.stencil_run(plan, u0, y, p.T)
+    g = (y - tg).contiguous()
+    gu, gw = sg.stencil_adjoint_run(plan, u0, g, p.T, p.extra["ckpt_every"])
+    gw = gw.cpu().numpy()
+    hw = 1e-5
+    for j in range(7):
+        wp = list(p.weights); wm = list(p.weights)
+        wp[j] += hw; wm[j] -= hw
+        # the FP32 weights the runs actually use
+        dw = float(np.float32(wp[j])) - float(np.float32(wm[j]))
+        fd = (loss(wp, u0) - loss(wm, u0)) / dw
+        assert abs(fd - gw[j]) <= 1e-2 * abs(gw[j]), (j, fd, gw[j])
+    h = 1e-3
+    gen = torch.Generator(device=DEV).manual_seed(3)
+    for _ in range(2):
+        dvec = torch.randn(p.shape, device=DEV, generator=gen)
+        fd = (loss(p.weights, u0 + h * dvec) - loss(p.weights, u0 - h * dvec)) / (2 * h)
+        an = float((gu.double() * dvec.double()).sum())
+        assert abs(fd - an) <= 1e-2 * abs(an) + 1e-2, (fd, an)
