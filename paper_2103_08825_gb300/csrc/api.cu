@@ -114,12 +114,14 @@ static stencil_status_t cuda_fail(cudaError_t e, const char *what) {
     return STENCIL_ERR_CUDA;
 }
 
+// 32 bytes: the status word at offset 0, two job-ticket counters at 16
 static stencil_status_t ensure_status_word(stencil_plan_s *P) {
     if (P->d_status) return STENCIL_OK;
-    cudaError_t e = cudaMalloc(&P->d_status, sizeof(int));
+    cudaError_t e = cudaMalloc(&P->d_status, 32);
     if (e != cudaSuccess) { P->d_status = nullptr; set_error("status word allocation failed"); return STENCIL_ERR_OOM; }
-    e = cudaMemset(P->d_status, 0, sizeof(int));
+    e = cudaMemset(P->d_status, 0, 32);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    P->d_ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(P->d_status) + 16);
     return STENCIL_OK;
 }
 

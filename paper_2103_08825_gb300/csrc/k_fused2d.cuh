@@ -66,6 +66,8 @@ template <typename C> struct F2Params {
     int64_t Ly;
     int vec_ok;        // rows and both base pointers allow V-wide vector access
     int *status;
+    unsigned long long *ctr;   // job tickets: this launch uses ctr[parity], resets the other
+    int parity;
     C w[25];           // evaluation order; up to the r = 2 box
 };
 
@@ -170,7 +172,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, NS = 2 * R;
     // step unroll: the partial-row slots repeat every 2R rows; the register
     // prefetch ring (PROD_REG) every F2_PREF rows
-    constexpr int U = PROD == PROD_TMA ? NS : F2_U;
+    constexpr int U = F2_U;
     static_assert(F2_ROWS % U == 0 && F2_U % NS == 0, "unroll");
     constexpr uint32_t FULLM = (1u << V) - 1u;
 
@@ -374,13 +376,20 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
         }
         __syncwarp();
     }
-    C wr[Sh::npts];
-#pragma unroll
-    for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
+    const C *wr = p.w;   // parameter space: FMAs can read the weights as constant operands
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
     uint32_t gst = 0;
-    for (int64_t job = (int64_t)blockIdx.x * F2_NW + warp; job < p.jobs; job += (int64_t)gridDim.x * F2_NW) {
-        const int64_t band = job % p.bands, chunk = job / p.bands;
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = 0ull;   // for the next launch
+    // jobs are taken dynamically, so faster SMs take more; the first and last
+    // row chunks (Dirichlet edges, the slower jobs) come first
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&p.ctr[p.parity], 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)p.jobs) break;
+        const int64_t band = (int64_t)(t % p.bands), tc = (int64_t)(t / p.bands);
+        const int64_t nch = p.jobs / p.bands;
+        const int64_t chunk = nch < 2 ? tc : (tc == 0 ? 0 : tc == 1 ? nch - 1 : tc - 1);
         const int64_t yo0 = chunk * p.Ly;
         const int64_t yo1 = yo0 + p.Ly < p.g.n1 ? yo0 + p.Ly : p.g.n1;
         const int64_t xo0 = band * G::BW;
@@ -422,6 +431,8 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.src = src;
     p.dst = dst;
     p.status = P.d_status;
+    p.ctr = P.d_ctr;
+    p.parity = (int)(P.job_seq++ & 1u);
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1];
     if (ny + 4 * R * K + 64 >= (1ll << 31)) return cudaErrorNotSupported;   // rows are 32-bit in the kernel
@@ -450,7 +461,7 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     const int64_t bands = (nx + G::BW - 1) / G::BW;
     const int64_t slots = (int64_t)P.sm_count * bps * F2_NW;
     const int64_t min_ly = 4 * R * K > 16 ? 4 * R * K : 16;
-    int64_t chunks = slots / bands;
+    int64_t chunks = 2 * slots / bands;   // about two jobs per resident warp
     if (chunks < 1) chunks = 1;
     const int64_t max_chunks = ny / min_ly > 1 ? ny / min_ly : 1;
     if (chunks > max_chunks) chunks = max_chunks;

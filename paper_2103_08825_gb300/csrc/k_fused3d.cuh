@@ -17,7 +17,7 @@
 //             the warps above and below through shared memory (one barrier
 //             per level); level-0 planes are read straight from the stage;
 //   input     PROD_TMA: warp 0 lane 0 loads whole window planes with 3D TMA
-//             into a 4-stage ring (mbarrier completion, bounded waits);
+//             into an 8-stage ring (mbarrier completion, bounded waits);
 //             PROD_CPASYNC: every thread copies its share of the plane with
 //             cp.async, indices wrapped (periodic grids, unaligned rows);
 //   halo      the window's outer H >= rK columns and rK rows are recomputed
@@ -35,7 +35,7 @@ namespace sg {
 constexpr int F3_NWY = 16;               // warps per CTA, stacked in y
 constexpr int F3_RY = 2;                 // window rows per warp
 constexpr int F3_WY = F3_NWY * F3_RY;    // window rows
-constexpr int F3_STAGES = 4;             // plane ring depth
+constexpr int F3_STAGES = 8;             // plane ring depth: ~112 KiB in flight per SM
 constexpr int F3_THREADS = F3_NWY * 32;
 enum { PROD3_TMA = 0, PROD3_CPASYNC = 1 };
 
@@ -65,6 +65,8 @@ template <typename C> struct F3Params {
     int64_t jobs, tiles_x, tiles_y, Lz;
     int vec_ok;
     int *status;
+    unsigned long long *ctr;   // job tickets: this launch uses ctr[parity], resets the other
+    int parity;
     C w[125];               // evaluation order; up to the r = 2 box
 };
 
@@ -236,7 +238,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     ldsvec<DT>(pl + wrow * W + lane * V, inc[j]);
                 }
                 if constexpr (MASK) {
-                    if (zin < 0 || zin >= nz) {                       // plane outside: uniform
+                    if ((uint32_t)zin >= (uint32_t)nz) {              // plane outside: uniform
 #pragma unroll
                         for (int j = 0; j < NR; ++j)
 #pragma unroll
@@ -244,8 +246,8 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     } else {
 #pragma unroll
                         for (int j = 0; j < NR; ++j) {
-                            const int64_t y = yw0 + row0 - R + j;     // warp-uniform
-                            if (y < 0 || y >= ny) {
+                            const int y = (int)yw0 + row0 - R + j;    // warp-uniform
+                            if ((uint32_t)y >= (uint32_t)ny) {
 #pragma unroll
                                 for (int v = 0; v < V; ++v) inc[j][v] = bval;
                             } else if (need_cmask) {
@@ -256,7 +258,18 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     }
                 }
             }
-            if constexpr (K == 1) __syncthreads();   // every warp has read the stage
+            if constexpr (K == 1) {
+                __syncthreads();   // every warp has read the stage: refill it now
+                if constexpr (PROD == PROD3_TMA) {
+                    if (threadIdx.x == 0 && i + F3_STAGES < nsp) {
+                        fence_proxy_async_smem();
+                        const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
+                        mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
+                        tma_load_3d(stages + (size_t)sl2 * G::PLANE, tmap, &bars[sl2], (int)xw0, (int)yw0,
+                                    (int)(zi0 + i + F3_STAGES));
+                    }
+                }
+            }
             // ---- C: K levels
 #pragma unroll
             for (int s = 0; s < K; ++s) {
@@ -323,9 +336,9 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                         }
                 }
                 // emitted plane index: Dirichlet cells keep the boundary value
-                const int64_t ze = zin - (int64_t)(s + 1) * R;
+                const int ze = (int)zin - (s + 1) * R;
                 if constexpr (MASK) {
-                    if (ze < 0 || ze >= nz) {                          // plane outside: uniform
+                    if ((uint32_t)ze >= (uint32_t)nz) {                // plane outside: uniform
 #pragma unroll
                         for (int j = 0; j < RY; ++j)
 #pragma unroll
@@ -333,8 +346,8 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     } else {
 #pragma unroll
                         for (int j = 0; j < RY; ++j) {
-                            const int64_t y = yw0 + row0 + j;          // warp-uniform
-                            if (y < 0 || y >= ny) {
+                            const int y = (int)yw0 + row0 + j;         // warp-uniform
+                            if ((uint32_t)y >= (uint32_t)ny) {
 #pragma unroll
                                 for (int v = 0; v < V; ++v) emit[j][v] = bval;
                             } else if (need_cmask) {
@@ -394,15 +407,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     }
                 }
             }
-            if constexpr (K == 1 && PROD == PROD3_TMA) {
-                if (threadIdx.x == 0 && i + F3_STAGES < nsp) {
-                    fence_proxy_async_smem();
-                    const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
-                    mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
-                    tma_load_3d(stages + (size_t)sl2 * G::PLANE, tmap, &bars[sl2], (int)xw0, (int)yw0,
-                                (int)(zi0 + i + F3_STAGES));
-                }
-            }
+
         }
         if (bad) break;
     }
@@ -450,9 +455,21 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
     uint32_t gst = 0;   // planes consumed so far by this CTA (stage ring position)
     int xpar = 0;       // exchange-buffer parity
-    for (int64_t job = blockIdx.x; job < p.jobs; job += gridDim.x) {
+    __shared__ unsigned long long s_ticket;
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = 0ull;   // for the next launch
+    // jobs are taken dynamically (faster SMs take more); the first and last z
+    // ranges (Dirichlet edges) come first
+    const int64_t nch = p.jobs / (p.tiles_x * p.tiles_y);
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctr[p.parity], 1ull);
+        __syncthreads();
+        const unsigned long long t = s_ticket;
+        __syncthreads();
+        if (t >= (unsigned long long)p.jobs) break;
+        const int64_t job = (int64_t)t;
         const int64_t tx = job % p.tiles_x, rest = job / p.tiles_x;
-        const int64_t ty = rest % p.tiles_y, cz = rest / p.tiles_y;
+        const int64_t ty = rest % p.tiles_y, tc = rest / p.tiles_y;
+        const int64_t cz = nch < 2 ? tc : (tc == 0 ? 0 : tc == 1 ? nch - 1 : tc - 1);
         const int64_t xo0 = tx * G::BW, yo0 = ty * G::BY;
         const int64_t zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
         // windows inside the domain never meet a Dirichlet cell: no masking code
@@ -486,6 +503,8 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.src = src;
     p.dst = dst;
     p.status = P.d_status;
+    p.ctr = P.d_ctr;
+    p.parity = (int)(P.job_seq++ & 1u);
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
     p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
@@ -516,18 +535,13 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.tiles_y = (ny + G::BY - 1) / G::BY;
     const int64_t tiles = p.tiles_x * p.tiles_y;
     const int64_t slots = (int64_t)P.sm_count * bps;
-    // z ranges: enough jobs for whole waves, each range >= 4 rK planes
+    // z ranges: about three jobs per resident CTA (taken dynamically), each
+    // range at least 4 rK planes long
     const int64_t min_lz = 4 * R * K > 8 ? 4 * R * K : 8;
-    int64_t best_c = 1;
-    double best_eff = 0.0;
-    for (int64_t c = 1; c <= 64; ++c) {
-        if (c > 1 && (nz + c - 1) / c < min_lz) break;
-        const int64_t jobs = tiles * c;
-        const int64_t waves = (jobs + slots - 1) / slots;
-        const double lz = (double)((nz + c - 1) / c);
-        const double eff = (double)jobs / (double)(waves * slots) * lz / (lz + 2.0 * R * K);
-        if (eff > best_eff + 1e-9) { best_eff = eff; best_c = c; }
-    }
+    int64_t best_c = (3 * slots + tiles - 1) / tiles;
+    if (best_c < 1) best_c = 1;
+    const int64_t max_c = nz / min_lz > 1 ? nz / min_lz : 1;
+    if (best_c > max_c) best_c = max_c;
     p.Lz = (nz + best_c - 1) / best_c;
     const int64_t chunks = (nz + p.Lz - 1) / p.Lz;
     p.jobs = tiles * chunks;

@@ -152,12 +152,13 @@ __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ Plai
     }
 }
 
-// The one-step sweep for grids whose every extent is >= r: a block owns RB
-// consecutive rows of one plane (its row and plane indices are uniform, so
-// rows outside the grid cost one uniform branch), each thread 4 x-points of
-// those rows.  Rows shared by the RB outputs are loaded once; x-halo values
-// at the grid's ends go through a predicated load (wrap by +-n, or the
-// boundary value), so no thread takes a divergent slow path.
+// The one-step sweep for grids with moderate extents (every extent > 2r + 2,
+// rows and planes addressable by the launch grid): one thread computes 4
+// x-points of RB consecutive rows of one plane.  Row and plane indices are
+// 32-bit and uniform across a warp's lanes, so rows outside the grid cost one
+// uniform branch; each row used is addressed once (one 64-bit pointer), rows
+// shared by the RB outputs are loaded once, and x-halo values at the grid's
+// ends go through a predicated load (wrap by +-n, or the boundary value).
 template <int DT, int D, int R, int PAT, int RB>
 __global__ void __launch_bounds__(256) plain_rows_kernel(const __grid_constant__ PlainParams<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
@@ -168,98 +169,91 @@ __global__ void __launch_bounds__(256) plain_rows_kernel(const __grid_constant__
     constexpr int NY = D >= 2 ? RB + 2 * R : 1;         // rows read per plane
     const S *__restrict__ src = static_cast<const S *>(p.src);
     S *__restrict__ dst = static_cast<S *>(p.dst);
-    const int64_t n0 = p.g.n0, n1 = p.g.n1, n2 = p.g.n2;
+    const int n0 = (int)p.g.n0, n1 = (int)p.g.n1, n2 = (int)p.g.n2;
     const bool periodic = p.g.bkind == STENCIL_PERIODIC;
     const C bval = p.g.bval;
-    const int64_t groups = (n2 + VX - 1) / VX;
-    for (int64_t i0 = blockIdx.z; i0 < n0; i0 += gridDim.z) {
-        for (int64_t i1b = ((int64_t)blockIdx.y * blockDim.y + threadIdx.y) * RB; i1b < n1;
-             i1b += (int64_t)gridDim.y * blockDim.y * RB) {
-            for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
-                 g += (int64_t)gridDim.x * blockDim.x) {
-                const int64_t x0 = g * VX;
-                const bool full = x0 + VX <= n2;
-                C val[NZ][NY][VX + 2 * R];
+    const int i0 = blockIdx.z;
+    const int i1b = (blockIdx.y * blockDim.y + threadIdx.y) * RB;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+    if (x0 >= n2 || i1b >= n1) return;
+    const bool full = x0 + VX <= n2;
+    C val[NZ][NY][VX + 2 * R];
 #pragma unroll
-                for (int jz = 0; jz < NZ; ++jz) {
-                    const int oz = D == 3 ? jz - R : 0;
+    for (int jz = 0; jz < NZ; ++jz) {
+        const int oz = D == 3 ? jz - R : 0;
 #pragma unroll
-                    for (int jy = 0; jy < NY; ++jy) {
-                        // is this row used, and does it need its x-halo?
-                        bool used = false, halo = false;
+        for (int jy = 0; jy < NY; ++jy) {
+            bool used = false, halo = false;
 #pragma unroll
-                        for (int b = 0; b < RB; ++b) {
-                            const int oy = D >= 2 ? jy - R - b : 0;
-                            if (D >= 2 && (oy < -R || oy > R)) continue;
-                            if (Sh::inc(oz, oy, 0)) used = true;
-                            if (PAT == STENCIL_BOX || (oz == 0 && oy == 0)) halo = true;
-                        }
-                        if (!used) continue;
-                        int64_t z = i0 + oz, y = D >= 2 ? i1b - R + jy : 0;
-                        bool ok = true;
-                        if (z < 0) { if (periodic) z += n0; else ok = false; }
-                        if (z >= n0) { if (periodic) z -= n0; else ok = false; }
-                        if (y < 0) { if (periodic) y += n1; else ok = false; }
-                        if (y >= n1) { if (periodic) y -= n1; else ok = false; }
-                        C *row = val[jz][jy];
-                        if (!ok) {
+            for (int b = 0; b < RB; ++b) {
+                const int oy = D >= 2 ? jy - R - b : 0;
+                if (D >= 2 && (oy < -R || oy > R)) continue;
+                if (Sh::inc(oz, oy, 0)) used = true;
+                if (PAT == STENCIL_BOX || (oz == 0 && oy == 0)) halo = true;
+            }
+            if (!used) continue;
+            int z = i0 + oz, y = D >= 2 ? i1b - R + jy : 0;
+            bool ok = true;
+            if (z < 0) { z += n0; ok = periodic; }
+            else if (z >= n0) { z -= n0; ok = periodic; }
+            if (y < 0) { y += n1; ok = ok && periodic; }
+            else if (y >= n1) { y -= n1; ok = ok && periodic; }
+            C *row = val[jz][jy];
+            if (!ok) {
 #pragma unroll
-                            for (int q = 0; q < VX + 2 * R; ++q) row[q] = bval;
-                            continue;
-                        }
-                        const S *rowp = src + (z * n1 + y) * n2;
-                        if (full && p.vec_ok) {
-                            ldg4<S, C>(rowp + x0, row + R);
-                        } else {
+                for (int q = 0; q < VX + 2 * R; ++q) row[q] = bval;
+                continue;
+            }
+            const S *rowp = src + ((int64_t)z * n1 + y) * n2;
+            if (full && p.vec_ok) {
+                ldg4<S, C>(rowp + x0, row + R);
+            } else {
 #pragma unroll
-                            for (int q = 0; q < VX; ++q) {   // last, partial group: wrap or boundary value
-                                const int64_t x = x0 + q;
-                                row[R + q] = x < n2 ? to_c(__ldg(rowp + x)) : (periodic ? to_c(__ldg(rowp + x - n2)) : bval);
-                            }
-                        }
-                        if (halo) {
-#pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                int64_t xl = x0 - R + q, xr = x0 + VX + q;
-                                const bool il = xl >= 0, ir = xr < n2;
-                                xl = il ? xl : xl + n2;
-                                xr = ir ? xr : xr - n2;
-                                row[q] = (il || periodic) ? to_c(__ldg(rowp + xl)) : bval;
-                                row[R + VX + q] = (ir || periodic) ? to_c(__ldg(rowp + xr)) : bval;
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                    const int64_t yo = D >= 2 ? i1b + b : 0;
-                    if (yo >= n1) break;
-                    C acc[VX];
-                    bool first = true;
-#pragma unroll
-                    for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz)
-#pragma unroll
-                        for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy)
-#pragma unroll
-                            for (int ox = -R; ox <= R; ++ox) {
-                                if (!Sh::inc(oz, oy, ox)) continue;
-                                const C w = p.w[Sh::widx(oz, oy, ox)];
-                                const C *row = val[D == 3 ? oz + R : 0][D >= 2 ? R + b + oy : 0];
-#pragma unroll
-                                for (int v = 0; v < VX; ++v)
-                                    acc[v] = first ? op_mul(w, row[R + v + ox]) : op_fma(w, row[R + v + ox], acc[v]);
-                                first = false;
-                            }
-                    S *out = dst + (i0 * n1 + yo) * n2;
-                    if (p.vec_ok && full) {
-                        st4<S, C>(out + x0, acc);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < VX; ++v)
-                            if (x0 + v < n2) out[x0 + v] = from_c<S>(acc[v]);
-                    }
+                for (int q = 0; q < VX; ++q) {   // last, partial group: wrap or boundary value
+                    const int x = x0 + q;
+                    row[R + q] = x < n2 ? to_c(__ldg(rowp + x)) : (periodic ? to_c(__ldg(rowp + x - n2)) : bval);
                 }
             }
+            if (halo) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    int xl = x0 - R + q, xr = x0 + VX + q;
+                    const bool il = xl >= 0, ir = xr < n2;
+                    xl = il ? xl : xl + n2;
+                    xr = ir ? xr : xr - n2;
+                    row[q] = (il || periodic) ? to_c(__ldg(rowp + xl)) : bval;
+                    row[R + VX + q] = (ir || periodic) ? to_c(__ldg(rowp + xr)) : bval;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+        const int yo = D >= 2 ? i1b + b : 0;
+        if (yo >= n1) break;
+        C acc[VX];
+        bool first = true;
+#pragma unroll
+        for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz)
+#pragma unroll
+            for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy)
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    if (!Sh::inc(oz, oy, ox)) continue;
+                    const C w = p.w[Sh::widx(oz, oy, ox)];
+                    const C *row = val[D == 3 ? oz + R : 0][D >= 2 ? R + b + oy : 0];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v)
+                        acc[v] = first ? op_mul(w, row[R + v + ox]) : op_fma(w, row[R + v + ox], acc[v]);
+                    first = false;
+                }
+        S *out = dst + ((int64_t)i0 * n1 + yo) * n2;
+        if (p.vec_ok && full) {
+            st4<S, C>(out + x0, acc);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v)
+                if (x0 + v < n2) out[x0 + v] = from_c<S>(acc[v]);
         }
     }
 }
@@ -298,16 +292,17 @@ static cudaError_t launch_plain_t(const stencil_plan_s &P, const void *src, void
     if (bx > (1ll << 30)) bx = 1ll << 30;
     // two rows per thread where the loaded rows stay few (all but the 3D box)
     constexpr int RB = (D >= 2 && !(D == 3 && PAT == STENCIL_BOX)) ? 2 : 1;
-    // wrapping by one extent must land inside the grid
-    const bool big = (D < 3 || P.n[0] > 2 * R + 2) && (D < 2 || P.n[1] > 2 * R + RB + 2) && P.n[2] >= 2 * (4 + R);
+    // block: TX threads along a row (the row's groups, up to 256), TY rows
+    const int tx = (int)std::min<int64_t>(256, (groups + 31) / 32 * 32);
+    const int ty = 256 / tx;
+    const int64_t bxr = (groups + tx - 1) / tx;
+    const int64_t rows = (P.n[1] + (int64_t)RB * ty - 1) / ((int64_t)RB * ty);
+    // wrapping by one extent must land inside the grid; the launch grid must
+    // cover every row and plane; 32-bit indices
+    const bool big = (D < 3 || P.n[0] > 2 * R + 2) && (D < 2 || P.n[1] > 2 * R + RB + 2) && P.n[2] >= 2 * (4 + R) &&
+                     P.n[0] <= 65535 && rows <= 65535 && P.n[2] < (1ll << 30) && P.n[1] < (1ll << 30);
     if (big) {
-        // block: TX threads along a row (the row's groups, up to 256), TY rows
-        int tx = (int)std::min<int64_t>(256, (groups + 31) / 32 * 32);
-        const int ty = 256 / tx;
-        const int64_t bxr = (groups + tx - 1) / tx;
-        const int64_t rows = (P.n[1] + (int64_t)RB * ty - 1) / ((int64_t)RB * ty);
-        const dim3 grid((unsigned)std::min<int64_t>(bxr, 1ll << 30), (unsigned)(rows < 65535 ? rows : 65535),
-                        (unsigned)(P.n[0] < 65535 ? P.n[0] : 65535));
+        const dim3 grid((unsigned)bxr, (unsigned)rows, (unsigned)P.n[0]);
         plain_rows_kernel<DT, D, R, PAT, RB><<<grid, dim3(tx, ty), 0, st>>>(p);
     } else {
         const dim3 grid((unsigned)bx, (unsigned)(P.n[1] < 65535 ? P.n[1] : 65535),

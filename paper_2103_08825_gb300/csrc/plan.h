@@ -33,6 +33,8 @@ struct stencil_plan_s {
     void *hws[2] = {nullptr, nullptr};   // device copies for stencil_run_host
     size_t grid_bytes = 0;
     int *d_status = nullptr;   // device status word (0 = OK)
+    unsigned long long *d_ctr = nullptr;   // two job-ticket counters (same allocation)
+    mutable unsigned job_seq = 0;          // launches that used the counters
     // adjoint workspace
     void *adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
