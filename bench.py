@@ -236,13 +236,107 @@ def workload_name(key, p):
     return f"{p.name} {shape} {dt} T={p.T} {bnd}"
 
 
+def _events_ms(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batch(args):
+    """Batched workload: 256 periodic 2D 9-point FP32 grids of uneven size and
+    step count in one graph-captured persistent launch, against one
+    stencil_run per grid on the same GPU."""
+    import torch
+    import paper_2103_08825_gb300 as sg
+    sg.load()
+    probs = synth.c4_batch()
+    xs = [torch.from_numpy(synth.uniform01(p.seed, p.npts).reshape(p.shape).astype(np.float32)).cuda() for p in probs]
+    ys = [torch.empty_like(x) for x in xs]
+    b = sg.stencil_batch_create([p.shape for p in probs], [p.weights for p in probs], [p.T for p in probs],
+                                synth.BOX, 1, synth.PERIODIC, 0.0, sg.STENCIL_F32)
+    upd = float(sum(p.npts * p.T for p in probs))
+    ms = _events_ms(lambda: sg.stencil_batch_run(b, xs, ys), args.steps, args.warmup)
+    if sg.stencil_batch_get_device_status(b) != 0:
+        raise RuntimeError("batch status word reports a timeout")
+    plans = [sg.stencil_plan_create(2, 1, p.shape, synth.BOX, p.weights, synth.PERIODIC, 0.0, sg.STENCIL_F32)
+             for p in probs]
+
+    def separate():
+        for pl, p, x, y in zip(plans, probs, xs, ys):
+            sg.stencil_run(pl, x, y, p.T)
+
+    ms_sep = _events_ms(separate, max(3, args.steps // 4), 2)
+    launches_sep = sum(sg.stencil_plan_launch_count(pl, p.T) for pl, p in zip(plans, probs))
+    peak, peak_kind = measured_peaks()
+    passes = sum(-(-p.T // 4) * p.npts for p in probs)      # k = 4 passes per grid
+    achieved = 2.0 * 4 * passes / (ms * 1e-3) / 1e9
+    line = {"metric": "batched GStencil/s, one persistent graph-captured launch vs one stencil_run per grid",
+            "value": upd / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (256 seeded grids, sides log-uniform 64..2048, T uniform 8..128, periodic)",
+            "config": {"workload": "batch 256 x 2d9p periodic F32", "grids": len(probs), "points": sum(p.npts for p in probs),
+                       "updates": upd, "k": 4},
+            "separate_runs": {"value": upd / (ms_sep * 1e-3) / 1e9, "ms_per_step": ms_sep, "launches": launches_sep},
+            "speedup_vs_separate": ms_sep / ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_step": 2.0 * 4 * passes},
+            "gpu_launches": args.steps * sg.stencil_batch_launch_count(b)}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """Differentiation workload: 3D 7-point periodic 256^3 FP32, T = 64,
+    checkpoints every 8: backward (stencil_adjoint_run) against forward."""
+    import torch
+    import paper_2103_08825_gb300 as sg
+    sg.load()
+    p = synth.c5_adjoint()
+    u0 = torch.from_numpy(synth.uniform01(p.seed, p.npts).reshape(p.shape).astype(np.float32)).cuda()
+    tg = torch.from_numpy(synth.uniform01(p.extra["target_seed"], p.npts).reshape(p.shape).astype(np.float32)).cuda()
+    plan = sg.stencil_plan_create(3, 1, p.shape, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_F32)
+    sg.stencil_plan_tune(plan, p.T)
+    y = torch.empty_like(u0)
+    gu = torch.empty_like(u0)
+    gw = torch.empty(7, dtype=torch.float64, device="cuda")
+    ms_f = _events_ms(lambda: sg.stencil_run(plan, u0, y, p.T), args.steps, args.warmup)
+    g = (y - tg).contiguous()
+    ms_b = _events_ms(lambda: sg.stencil_adjoint_run(plan, u0, g, p.T, p.extra["ckpt_every"], gu, gw),
+                      max(3, args.steps // 4), 2)
+    upd = float(p.npts) * p.T
+    peak, peak_kind = measured_peaks()
+    # backward bytes: checkpoint forward (fused) + recompute (one step each)
+    # + adjoint steps (read lam and u, write lam: 12 bytes per point)
+    c = p.extra["ckpt_every"]
+    bytes_adj = p.npts * p.T * 12.0
+    line = {"metric": "adjoint GStencil/s (backward, checkpointed) and backward/forward time",
+            "value": upd / (ms_b * 1e-3) / 1e9, "unit": "GStencil/s", "n_gpus": 1, "dtype": "f32",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "data": "synthetic (seeded uniform[0,1) u0 and target)",
+            "config": {"workload": "3d7p 256^3 periodic F32 T=64 ckpt 8", "k_forward": sg.stencil_plan_get_k(plan)},
+            "forward": {"value": upd / (ms_f * 1e-3) / 1e9, "ms_per_step": ms_f},
+            "backward_over_forward": ms_b / ms_f,
+            "adjoint_step_bytes": bytes_adj, "ckpt_every": c,
+            "roofline_adjoint_steps_only": {"bound": "hbm", "bytes_per_step": bytes_adj, "peak": peak,
+                                            "peak_kind": peak_kind}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d5p", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="2d5p", choices=sorted(WORKLOADS) + ["batch", "adjoint"])
     ap.add_argument("--k", type=int, default=0, help="fusion depth (0 = autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=0, help="steps for the plain sweep (0 = steps/4)")
@@ -255,6 +349,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
 
     import torch
