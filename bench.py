@@ -449,17 +449,21 @@ def main():
         sg.stencil_plan_set_variant(plan, sg.STENCIL_VARIANT_FUSED)
         sg.stencil_plan_set_k(plan, k)
 
-    # roofline of the dominant (fused) kernel: algorithmic bytes per launch
-    # (one read and one write of every point) / average launch duration
+    # roofline of the fused sweep: algorithmic bytes (one read and one write
+    # of every point per pass of k steps) over the timed step.  With the 2D
+    # persistent kernel one launch carries every pass of exactly k steps, so
+    # when T is a multiple of k the step is that single launch.
     peak, peak_kind = measured_peaks()
-    bytes_launch = 2.0 * p.npts * esize
-    avg_launch_s = ms_step * 1e-3 / launches
-    achieved = bytes_launch / avg_launch_s / 1e9
+    fused_now = not (tuned is not None and tuned[0] == 0)
+    passes = -(-p.T // k) if fused_now else p.T
+    bytes_step = 2.0 * p.npts * esize * passes
+    achieved = bytes_step / (ms_step * 1e-3) / 1e9
     key = f"{args.workload}:k{k}:{kernel_hash()}"
     traffic = NCU_TRAFFIC.get(key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": sg.stencil_plan_describe(plan),
-                "bytes_per_launch": bytes_launch, "launches_per_step": launches}
+                "bytes_per_launch": bytes_step / launches, "bytes_per_pass": 2.0 * p.npts * esize,
+                "passes_per_step": passes, "launches_per_step": launches}
 
     # error at the timed configuration: a Dirichlet sine mode must decay by
     # lam^T (closed form, no oracle involved)
@@ -513,7 +517,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtn, "data": "synthetic (seeded uniform[0,1), fixed boundary)",
             "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T, "k": k,
-                       "tuned": {"k": tuned[0], "ms": tuned[1]} if tuned else None,
+                       "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan)}
+                       if tuned else None,
                        "l2": f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "plain_sweep": {"value": plain_value, "unit": "GStencil/s", "ms_per_step": ms_plain,

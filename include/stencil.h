@@ -70,9 +70,16 @@ typedef enum { STENCIL_STAR = 0, STENCIL_BOX = 1 } stencil_pattern_t;
 typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_kind_t;
 
 /* Which kernels stencil_run uses.  FUSED: k steps per pass (the default);
+ * for 2D grids the passes of exactly k steps run as one persistent launch
+ * whose tiles wait on their neighbours' completion of the previous pass.
  * PLAIN: one step per launch, each thread reading its own neighbours -- the
- * one-step-per-launch sweep the fused path is measured against. */
-typedef enum { STENCIL_VARIANT_FUSED = 0, STENCIL_VARIANT_PLAIN = 1 } stencil_variant_t;
+ * one-step-per-launch sweep the fused path is measured against.
+ * FUSED_PER_PASS: the fused kernels with one launch per pass. */
+typedef enum {
+    STENCIL_VARIANT_FUSED = 0,
+    STENCIL_VARIANT_PLAIN = 1,
+    STENCIL_VARIANT_FUSED_PER_PASS = 2
+} stencil_variant_t;
 
 /* Stencil coefficients: `count` values in compact order (see above). */
 typedef struct {
@@ -107,20 +114,30 @@ stencil_status_t stencil_plan_get_k(stencil_plan_t plan, int32_t *k);
 /* Largest k the fused kernels accept for this plan. */
 stencil_status_t stencil_plan_max_k(stencil_plan_t plan, int32_t *kmax);
 
-/* Select FUSED (default) or PLAIN kernels for stencil_run. */
+/* Select FUSED (default), PLAIN or FUSED_PER_PASS kernels for stencil_run. */
 stencil_status_t stencil_plan_set_variant(stencil_plan_t plan, int32_t variant);
 
-/* Autotune the fusion depth: times stencil_run for the one-step kernel and
- * for every supported k on plan-owned buffers holding zeros, with CUDA events
- * on `stream`, and keeps the fastest (for tiny or FP64-pipe-bound grids the
+/* Tile height of the fused 2D kernels: the rows (outermost dimension) one
+ * warp job advances; at least max(4 r k, 16) and at most the grid's rows
+ * are used.  0 selects the default (about two jobs per resident warp per
+ * pass).  1D and 3D plans keep the value and ignore it. */
+stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t plan, int32_t rows);
+stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t plan, int32_t *rows);
+
+/* Autotune the fusion depth and (2D) the tile height: times stencil_run for
+ * the one-step kernel and for every supported k -- in 2D with each of a few
+ * tile heights -- on plan-owned buffers holding zeros, with CUDA events on
+ * `stream`, and keeps the fastest (for tiny or FP64-pipe-bound grids the
  * one-step kernel can win).  Synchronises `stream`.  `T` is the step count to
  * tune for; best_k (may be NULL) receives the chosen k, or 0 when the
- * one-step kernel won; best_ms (may be NULL) its time.  stencil_plan_set_k
- * and stencil_plan_set_variant discard the choice. */
+ * one-step kernel won; best_ms (may be NULL) its time; the chosen tile
+ * height is read with stencil_plan_get_tile_rows.  stencil_plan_set_k and
+ * stencil_plan_set_variant discard the choice of kernel. */
 stencil_status_t stencil_plan_tune(stencil_plan_t plan, int64_t T, void *stream, int32_t *best_k, double *best_ms);
 
 /* Number of kernel launches stencil_run makes for T steps with the current
- * variant and k (ceil(T/k) fused passes, or T plain steps). */
+ * variant and k: T plain steps, ceil(T/k) fused passes, or for the 2D
+ * persistent form one launch plus one for a last pass of T mod k steps. */
 stencil_status_t stencil_plan_launch_count(stencil_plan_t plan, int64_t T, int64_t *launches);
 
 /* Short text naming the kernel, k and tiling the plan uses (for logs). */

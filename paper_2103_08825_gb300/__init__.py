@@ -22,13 +22,14 @@ STENCIL_ERR_CUDA, STENCIL_ERR_TIMEOUT, STENCIL_ERR_INTERNAL = 4, 5, 6
 STENCIL_F64, STENCIL_F32, STENCIL_BF16, STENCIL_F16, STENCIL_I32 = 0, 1, 2, 3, 4
 STENCIL_STAR, STENCIL_BOX = 0, 1
 STENCIL_DIRICHLET, STENCIL_PERIODIC = 0, 1
-STENCIL_VARIANT_FUSED, STENCIL_VARIANT_PLAIN = 0, 1
+STENCIL_VARIANT_FUSED, STENCIL_VARIANT_PLAIN, STENCIL_VARIANT_FUSED_PER_PASS = 0, 1, 2
 STENCIL_REDUCE_SUM, STENCIL_REDUCE_SUMSQ, STENCIL_REDUCE_HALF_SQDIST = 0, 1, 2
 
 # Every symbol include/stencil.h declares (checked by the CPU test suite).
 EXPORTS = [
     "stencil_plan_create", "stencil_plan_destroy", "stencil_plan_set_k", "stencil_plan_get_k",
-    "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_tune", "stencil_plan_launch_count",
+    "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_set_tile_rows", "stencil_plan_get_tile_rows",
+    "stencil_plan_tune", "stencil_plan_launch_count",
     "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_batch_create",
     "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status",
     "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_reduce", "stencil_reduce_noalloc",
@@ -73,6 +74,8 @@ def load(path: str | None = None):
         "stencil_plan_get_k": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_max_k": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_set_variant": (st, [vp, i32]),
+        "stencil_plan_set_tile_rows": (st, [vp, i32]),
+        "stencil_plan_get_tile_rows": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_tune": (st, [vp, i64, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
         "stencil_plan_launch_count": (st, [vp, i64, ctypes.POINTER(i64)]),
         "stencil_plan_describe": (st, [vp, ctypes.c_char_p, i32]),
@@ -181,6 +184,16 @@ def stencil_plan_max_k(plan: Plan) -> int:
 
 def stencil_plan_set_variant(plan: Plan, variant: int):
     _check(load().stencil_plan_set_variant(plan.handle, int(variant)), "stencil_plan_set_variant")
+
+
+def stencil_plan_set_tile_rows(plan: Plan, rows: int):
+    _check(load().stencil_plan_set_tile_rows(plan.handle, int(rows)), "stencil_plan_set_tile_rows")
+
+
+def stencil_plan_get_tile_rows(plan: Plan) -> int:
+    r = ctypes.c_int32()
+    _check(load().stencil_plan_get_tile_rows(plan.handle, ctypes.byref(r)), "stencil_plan_get_tile_rows")
+    return r.value
 
 
 def stencil_plan_tune(plan: Plan, T: int, stream=None):

@@ -125,6 +125,26 @@ static stencil_status_t ensure_status_word(stencil_plan_s *P) {
     return STENCIL_OK;
 }
 
+cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t st) {
+    if (P.d_mp && tiles <= P.mp_tiles_cap) return cudaSuccess;
+    if (P.d_mp) {
+        cudaFree(P.d_mp);   // synchronises the device: no launch still uses it
+        P.d_mp = nullptr;
+        P.mp_tiles_cap = 0;
+    }
+    const size_t bytes = 2 * kMpCtlBytes + 2 * sizeof(int) * (size_t)tiles;
+    cudaError_t e = cudaMalloc(&P.d_mp, bytes);
+    if (e != cudaSuccess) {
+        P.d_mp = nullptr;
+        return e;
+    }
+    e = cudaMemsetAsync(P.d_mp, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+    P.mp_tiles_cap = tiles;
+    P.mp_seq = 0;
+    return cudaSuccess;
+}
+
 static stencil_status_t ensure_buf(void **buf, size_t bytes) {
     if (*buf) return STENCIL_OK;
     cudaError_t e = cudaMalloc(buf, bytes > 0 ? bytes : 16);
@@ -145,7 +165,16 @@ static int effective_k(const stencil_plan_s *P) {
 }
 
 static bool uses_fused(const stencil_plan_s *P) {
-    return P->variant == STENCIL_VARIANT_FUSED && !P->tuned_plain && fused_max_k(*P) > 0;
+    return (P->variant == STENCIL_VARIANT_FUSED || P->variant == STENCIL_VARIANT_FUSED_PER_PASS) && !P->tuned_plain &&
+           fused_max_k(*P) > 0;
+}
+
+// passes of exactly k steps that stencil_run gives one persistent launch
+// (0: one launch per pass)
+static int64_t multi_passes(const stencil_plan_s *P, int k, int64_t T) {
+    if (P->variant != STENCIL_VARIANT_FUSED || P->dim != 2 || !fused2d_multi_ok(*P, k)) return 0;
+    const int64_t full = T / k;
+    return full >= 2 && full <= (1 << 30) ? full : 0;
 }
 
 }  // namespace sg
@@ -257,6 +286,7 @@ stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
     cudaFree(P->d_status);
     cudaFree(P->adj_ws);
     cudaFree(P->adj_partials);
+    cudaFree(P->d_mp);
     cudaSetDevice(cur);
     delete P;
     return STENCIL_OK;
@@ -287,7 +317,8 @@ stencil_status_t stencil_plan_max_k(stencil_plan_t P, int32_t *kmax) {
 }
 
 stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
-    if (!P || (variant != STENCIL_VARIANT_FUSED && variant != STENCIL_VARIANT_PLAIN)) {
+    if (!P || (variant != STENCIL_VARIANT_FUSED && variant != STENCIL_VARIANT_PLAIN &&
+               variant != STENCIL_VARIANT_FUSED_PER_PASS)) {
         set_error("invalid plan or variant");
         return STENCIL_ERR_INVALID_ARG;
     }
@@ -296,12 +327,25 @@ stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
     return STENCIL_OK;
 }
 
+stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t P, int32_t rows) {
+    if (!P || rows < 0) { set_error("invalid plan or tile height"); return STENCIL_ERR_INVALID_ARG; }
+    P->tile_rows = rows;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t P, int32_t *rows) {
+    if (!P || !rows) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *rows = P->tile_rows;
+    return STENCIL_OK;
+}
+
 stencil_status_t stencil_plan_launch_count(stencil_plan_t P, int64_t T, int64_t *launches) {
     if (!P || !launches || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
     if (T == 0) { *launches = 0; return STENCIL_OK; }
     if (!uses_fused(P)) { *launches = T; return STENCIL_OK; }
     const int k = effective_k(P);
-    *launches = (T + k - 1) / k;
+    const int64_t mp = multi_passes(P, k, T);
+    *launches = mp > 0 ? 1 + (T - mp * k > 0 ? 1 : 0) : (T + k - 1) / k;
     return STENCIL_OK;
 }
 
@@ -336,7 +380,22 @@ stencil_status_t stencil_run(stencil_plan_t P, const void *u_in, void *u_out, in
         if (s != STENCIL_OK) return s;
     }
     const void *src = u_in;
-    for (int64_t p = 0; p < passes; ++p) {
+    int64_t p0 = 0;
+    const int64_t mp = fused ? multi_passes(P, k, T) : 0;
+    if (mp > 0) {
+        // passes 0..mp-1 in one persistent launch; its last pass lands where
+        // pass mp-1 of the loop below would
+        void *de = ((passes - mp) % 2 == 0) ? u_out : P->ws;
+        void *dof = de == u_out ? P->ws : u_out;
+        cudaError_t e = launch_fused2d_multi(*P, u_in, de, dof, k, (int)mp, st);
+        if (e == cudaSuccess) {
+            p0 = mp;
+            src = de;
+        } else if (e != cudaErrorNotSupported) {
+            return cuda_fail(e, "multi-pass kernel launch");
+        }
+    }
+    for (int64_t p = p0; p < passes; ++p) {
         // the last pass lands in u_out; earlier ones alternate ws / u_out
         void *dst = ((passes - 1 - p) % 2 == 0) ? u_out : P->ws;
         const int kp = (int)std::min<int64_t>(k, T - p * k);
@@ -380,35 +439,50 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved = P->k;
-    int bk = 1;
+    const int saved = P->k, saved_rows = P->tile_rows;
+    int bk = 1, brows = saved_rows;
     float bms = 1e30f;
     bool best_plain = false;
+    // tile heights tried in 2D: the default and a few fixed heights below
+    // the grid's row count (duplicates of the clamped maximum are skipped)
+    std::vector<int> rows_c = {0};
+    if (P->dim == 2)
+        for (int r : {32, 48, 64, 96, 128, 192})
+            if (r < P->n[1]) rows_c.push_back(r);
     // candidates: the one-step kernel (k = 0 here), then every fused depth
-    for (int k = 0; k <= km; ++k) {
-        P->tuned_plain = (k == 0);
-        P->k = k == 0 ? 1 : k;
-        s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
-        if (s != STENCIL_OK) break;
-        float best_rep = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(e0, st);
-            s = stencil_run(P, P->hws[0], P->hws[1], T, stream);
-            cudaEventRecord(e1, st);
+    for (int k = 0; k <= km && s == STENCIL_OK; ++k) {
+        for (size_t ri = 0; ri < (k == 0 ? 1 : rows_c.size()); ++ri) {
+            P->tuned_plain = (k == 0);
+            P->k = k == 0 ? 1 : k;
+            P->tile_rows = rows_c[ri];
+            s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
             if (s != STENCIL_OK) break;
-            e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) { s = cuda_fail(e, "tuning run"); break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            best_rep = std::min(best_rep, ms);
+            float best_rep = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                s = stencil_run(P, P->hws[0], P->hws[1], T, stream);
+                cudaEventRecord(e1, st);
+                if (s != STENCIL_OK) break;
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { s = cuda_fail(e, "tuning run"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best_rep = std::min(best_rep, ms);
+            }
+            if (s != STENCIL_OK) break;
+            if (best_rep < bms) {
+                bms = best_rep;
+                bk = k == 0 ? 1 : k;
+                best_plain = (k == 0);
+                brows = rows_c[ri];
+            }
         }
-        if (s != STENCIL_OK) break;
-        if (best_rep < bms) { bms = best_rep; bk = k == 0 ? 1 : k; best_plain = (k == 0); }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (s != STENCIL_OK) { P->k = saved; P->tuned_plain = false; return s; }
+    if (s != STENCIL_OK) { P->k = saved; P->tile_rows = saved_rows; P->tuned_plain = false; return s; }
     P->k = bk;
+    P->tile_rows = best_plain ? saved_rows : brows;
     P->tuned_plain = best_plain;
     if (best_k) *best_k = best_plain ? 0 : bk;
     if (best_ms) *best_ms = bms;

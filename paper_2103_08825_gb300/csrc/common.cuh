@@ -186,6 +186,60 @@ __device__ __forceinline__ void record_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------- cross-CTA completion counters
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// orders this thread's generic-proxy global accesses with its async-proxy
+// (TMA) ones: taken after acquiring data that other CTAs stored and before
+// reading it by TMA, and after storing data that other CTAs will read by TMA
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Wait until *ctr >= target (acquire), the abort flag rises, or about one
+// second of wall time passes; false unless the target was reached.
+__device__ __forceinline__ bool wait_counter(const int *ctr, int target, const int *abort_flag) {
+    if (ld_acquire(ctr) >= target) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_relaxed(abort_flag)) return false;
+        if (global_ns() - t0 > 1000000000ull) return false;
+        __nanosleep(it < 16 ? 32 : 256);
+    }
+    return false;
+}
+
+// The tiles along one axis (tile t covers [t len, min((t+1) len, n))) whose
+// range meets the coordinate range [lo, hi): the clipped range, plus for a
+// periodic axis its images wrapped from below and above.  Three intervals of
+// tile indices, some possibly empty or overlapping; requires -n <= lo and
+// hi <= 2n.
+struct TileSpan {
+    int a0, n0, a1, n1, a2, n2;
+    __device__ __forceinline__ int count() const { return n0 + n1 + n2; }
+    __device__ __forceinline__ int at(int i) const { return i < n0 ? a0 + i : i < n0 + n1 ? a1 + i - n0 : a2 + i - n0 - n1; }
+};
+
+__device__ __forceinline__ TileSpan tile_span(int lo, int hi, int n, int len, bool periodic) {
+    TileSpan s{0, 0, 0, 0, 0, 0};
+    const int c0 = lo > 0 ? lo : 0, c1 = hi < n ? hi : n;
+    if (c0 < c1) { s.a0 = c0 / len; s.n0 = (c1 - 1) / len + 1 - s.a0; }
+    if (periodic && lo < 0) { s.a1 = (lo + n) / len; s.n1 = (n - 1) / len + 1 - s.a1; }
+    if (periodic && hi > n) { s.a2 = 0; s.n2 = (hi - n - 1) / len + 1; }
+    return s;
+}
+
 __host__ __device__ constexpr int round_up_c(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ constexpr int max_c(int a, int b) { return a > b ? a : b; }
 

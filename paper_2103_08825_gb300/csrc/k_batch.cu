@@ -66,31 +66,6 @@ template <typename C> struct BatchParams {
     int *test_skip_publish;            // test hook: never publish this item (host-side fault injection)
 };
 
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_relaxed(const int *p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Wait until counter >= target, the abort flag rises, or ~1 s passes.
-__device__ __forceinline__ bool wait_counter(const int *ctr, int target, const int *abort_flag) {
-    if (ld_acquire(ctr) >= target) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (ld_acquire(ctr) >= target) return true;
-        if (ld_relaxed(abort_flag)) return false;
-        if (global_ns() - t0 > 1000000000ull) return false;
-        __nanosleep(it < 16 ? 32 : 256);
-    }
-    return false;
-}
-
 template <int DT, int R, int PAT, int K, int KB, bool MASK>
 __device__ __forceinline__ void batch_job(const BatchGrid<typename Traits<DT>::C> &G, const void *src, void *dst,
                                           bool dir, typename Traits<DT>::C bval,

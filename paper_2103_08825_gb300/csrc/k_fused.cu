@@ -1,5 +1,6 @@
 // k_fused.cu -- dispatch of one fused pass (k time steps) to the kernel for
 // the plan's dimension and storage type.
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -9,6 +10,7 @@ namespace sg {
 
 #define SG_DECL_F2(DT)                                                                              \
     cudaError_t launch_f2_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);   \
+    cudaError_t launch_f2mp_##DT(const stencil_plan_s &, const void *, void *, void *, int, int, cudaStream_t); \
     int f2_kmax_##DT(int r);                                                                        \
     int f2_bw_##DT(int r, int k);
 SG_DECL_F2(F32)
@@ -41,6 +43,31 @@ cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, 
     return cudaErrorInvalidValue;
 }
 
+// The multi-pass kernel needs halos that wrap at most once (periodic) and
+// coordinates, tiles and items that fit its 32-bit arithmetic.
+bool fused2d_multi_ok(const stencil_plan_s &P, int k) {
+    if (P.dim != 2 || k < 1 || k > fused2d_max_k(P)) return false;
+    const int v = P.dtype == STENCIL_F64 ? 2 : 4;
+    const int al = std::max(16 / (int)dtype_size(P.dtype), v);
+    const int64_t h = (P.r * k + al - 1) / al * al, w = 32 * v;
+    const int64_t nx = P.n[2], ny = P.n[1];
+    if (nx + 2 * w >= (1ll << 30) || ny + 4 * P.r * k + 64 >= (1ll << 30)) return false;
+    if (P.bkind == STENCIL_PERIODIC && (h > nx || P.r * k > ny)) return false;
+    return true;
+}
+
+cudaError_t launch_fused2d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                                 int passes, cudaStream_t st) {
+    switch (P.dtype) {
+        case STENCIL_F32: return launch_f2mp_F32(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_F64: return launch_f2mp_F64(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_BF16: return launch_f2mp_BF16(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_F16: return launch_f2mp_F16(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_I32: return launch_f2mp_I32(P, src0, dst_even, dst_odd, k, passes, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 std::string fused2d_describe(const stencil_plan_s &P, int k) {
     int bw = 0;
     switch (P.dtype) {
@@ -50,7 +77,8 @@ std::string fused2d_describe(const stencil_plan_s &P, int k) {
         case STENCIL_F16: bw = f2_bw_F16(P.r, k); break;
         case STENCIL_I32: bw = f2_bw_I32(P.r, k); break;
     }
-    return "fused2d(warp-streamed rows, k=" + std::to_string(k) + ", band=" + std::to_string(bw) + " cols)";
+    return "fused2d(warp-streamed rows, k=" + std::to_string(k) + ", band=" + std::to_string(bw) + " cols, tile rows=" +
+           (P.tile_rows > 0 ? std::to_string(P.tile_rows) : std::string("default")) + ")";
 }
 
 #define SG_DECL_F3(DT) cudaError_t launch_f3_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);

@@ -71,6 +71,33 @@ template <typename C> struct F2Params {
     C w[25];           // evaluation order; up to the r = 2 box
 };
 
+// Control block of a persistent multi-pass launch: the item ticket and the
+// abort flag raised when a dependency wait gives up.
+struct MpCtl {
+    unsigned long long ticket;
+    int abort;
+    int pad;
+};
+
+static_assert(sizeof(MpCtl) == kMpCtlBytes, "control block layout");
+
+template <typename C> struct F2MpParams {
+    GridGeom<C> g;     // n0 = 1, n1 = ny, n2 = nx
+    const void *src0;  // input of pass 0
+    void *dst_even;    // output of the passes p with (passes - 1 - p) even (includes the last)
+    void *dst_odd;     // output of the other passes
+    int passes;
+    int bands, chunks, Ly;
+    int vec_ok;
+    int *status;
+    MpCtl *ctl;        // [2]; this launch uses ctl[parity], clears ctl[parity ^ 1]
+    int *done;         // [2][cap]: passes each tile has finished (same parity rule;
+                       // the whole other half is cleared, whatever its next tiling)
+    int tiles, cap;
+    int parity;
+    C w[25];
+};
+
 // ------------------------------------------------------------ memory helpers
 template <bool COH, typename T> __device__ __forceinline__ T ldx(const T *p) {
     if constexpr (COH) return __ldcg(p);
@@ -411,10 +438,147 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     }
 }
 
+// All `passes` passes of stencil_run (K steps each) in one persistent launch.
+// Warps take (pass, tile) items from one ticket, pass-major and row-major
+// within a pass.  Before an item of pass p starts, every tile whose output
+// meets its input window must have finished pass p - 1: those are the tiles
+// whose outputs it reads and, since the relation is symmetric, the tiles whose
+// inputs (the buffer pass p + 1 ... reuses) its output overwrites -- so each
+// item reads finished data and never overwrites data still being read.
+// Every dependency has an earlier ticket, held by a running warp, so the
+// waits end; they are still bounded (about one second), and a wait that gives
+// up raises the abort flag, stops every warp and records STENCIL_ERR_TIMEOUT.
+// The per-pass tail of the one-launch-per-pass form (warps idle while the
+// last jobs of a pass finish) then occurs once per run.
+template <int DT, int R, int PAT, int K, int PROD>
+__global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
+    fused2d_mp_kernel(const __grid_constant__ CUtensorMap tm_src0, const __grid_constant__ CUtensorMap tm_even,
+                      const __grid_constant__ CUtensorMap tm_odd, const __grid_constant__ F2MpParams<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F2Geo<DT, R, K>;
+    constexpr bool COH = PROD == PROD_REG;   // register loads must bypass L1: other SMs wrote the data
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S *stg = reinterpret_cast<S *>(smem + warp * G::WARP_SMEM);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F2_NW * G::WARP_SMEM) + warp * F2_STAGES;
+    if constexpr (PROD == PROD_TMA) {
+        if (lane == 0) {
+            for (int s = 0; s < F2_STAGES; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+            prefetch_tmap(&tm_src0);
+            prefetch_tmap(&tm_even);
+            prefetch_tmap(&tm_odd);
+        }
+        __syncwarp();
+    }
+    // clear the other parity's counters for the next launch (stream-ordered)
+    {
+        int *other = p.done + (size_t)(p.parity ^ 1) * p.cap;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.cap; i += gridDim.x * blockDim.x) other[i] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            p.ctl[p.parity ^ 1].ticket = 0ull;
+            p.ctl[p.parity ^ 1].abort = 0;
+        }
+    }
+    MpCtl *ctl = p.ctl + p.parity;
+    int *done = p.done + (size_t)p.parity * p.cap;
+    const C *wr = p.w;
+    const bool dir = p.g.bkind == STENCIL_DIRICHLET;
+    const int nx = (int)p.g.n2, ny = (int)p.g.n1;
+    const int jobs = p.bands * p.chunks;
+    const unsigned long long items = (unsigned long long)jobs * (unsigned)p.passes;
+    uint32_t gst = 0;
+    for (;;) {
+        unsigned long long t = 0;
+        int ab = 0;
+        if (lane == 0) {
+            t = atomicAdd(&ctl->ticket, 1ull);
+            ab = ld_relaxed(&ctl->abort);
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        ab = __shfl_sync(0xffffffffu, ab, 0);
+        if (t >= items || ab) break;
+        const int pass = (int)(t / (unsigned)jobs), j = (int)(t % (unsigned)jobs);
+        const int chunk = j / p.bands, band = j - chunk * p.bands;
+        const int yo0 = chunk * p.Ly;
+        const int yo1 = yo0 + p.Ly < ny ? yo0 + p.Ly : ny;
+        const int xo0 = band * G::BW;
+        if (pass > 0) {
+            const int xe = xo0 + G::BW < nx ? xo0 + G::BW : nx;
+            const TileSpan sb = tile_span(xo0 - G::H, xe + G::H, nx, G::BW, !dir);
+            const TileSpan sc = tile_span(yo0 - R * K, yo1 + R * K, ny, p.Ly, !dir);
+            const int nb = sb.count(), nd = nb * sc.count();
+            bool ok = true;
+            for (int e = lane; e < nd; e += 32) {
+                const int b2 = sb.at(e % nb), c2 = sc.at(e / nb);
+                ok = ok && wait_counter(&done[c2 * p.bands + b2], pass, &ctl->abort);
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    atomicExch(&ctl->abort, 1);
+                    record_status(p.status, kStatusTimeout);
+                }
+                return;
+            }
+            __threadfence();
+            if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
+        }
+        const bool from_even = ((p.passes - pass) & 1) == 0;   // pass - 1 wrote dst_even
+        const S *src = static_cast<const S *>(pass == 0 ? p.src0 : from_even ? p.dst_even : p.dst_odd);
+        const CUtensorMap *tm = pass == 0 ? &tm_src0 : from_even ? &tm_even : &tm_odd;
+        S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
+        const bool interior = !dir || (xo0 - G::H >= 0 && xo0 - G::H + G::W <= nx && yo0 - R * K >= 0 &&
+                                       yo1 + R * K <= ny);
+        const bool ok = interior
+            ? fused2d_job<DT, R, PAT, K, PROD, COH, false>(tm, src, dst, nx, ny, dir, p.g.bval, wr, xo0, yo0, yo1,
+                                                          p.vec_ok != 0, stg, bars, gst, lane)
+            : fused2d_job<DT, R, PAT, K, PROD, COH, true>(tm, src, dst, nx, ny, dir, p.g.bval, wr, xo0, yo0, yo1,
+                                                         p.vec_ok != 0, stg, bars, gst, lane);
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(&ctl->abort, 1);
+                record_status(p.status, kStatusTimeout);
+            }
+            return;
+        }
+        // publish: this warp's stores, then the tile's pass count
+        __syncwarp();
+        if (lane == 0) {
+            if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
+            __threadfence();
+            atomicAdd(&done[j], 1);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 template <typename C> C conv_w(double w) {
     if constexpr (sizeof(C) == 4 && C(-1) > C(0)) return (C)(uint32_t)(int64_t)w;
     else return (C)w;
+}
+
+// Column bands of BW and row chunks of Ly: `rows` high if set, else about
+// `per_slot` jobs per resident warp; chunks at least max(4 r k, 16) rows.
+struct F2Tiling {
+    int64_t bands, chunks, Ly;
+};
+inline F2Tiling f2_tiling(int64_t nx, int64_t ny, int bw, int rk, int64_t slots, int per_slot, int rows) {
+    F2Tiling t;
+    t.bands = (nx + bw - 1) / bw;
+    const int64_t min_ly = 4 * rk > 16 ? 4 * rk : 16;
+    if (rows > 0) {
+        t.Ly = rows > min_ly ? rows : min_ly;
+        if (t.Ly > ny) t.Ly = ny;
+    } else {
+        int64_t chunks = per_slot * slots / t.bands;
+        if (chunks < 1) chunks = 1;
+        const int64_t max_chunks = ny / min_ly > 1 ? ny / min_ly : 1;
+        if (chunks > max_chunks) chunks = max_chunks;
+        t.Ly = (ny + chunks - 1) / chunks;
+    }
+    t.chunks = (ny + t.Ly - 1) / t.Ly;
+    return t;
 }
 
 template <int DT, int R, int PAT, int K>
@@ -458,20 +622,80 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F2_NW * 32, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    const int64_t bands = (nx + G::BW - 1) / G::BW;
-    const int64_t slots = (int64_t)P.sm_count * bps * F2_NW;
-    const int64_t min_ly = 4 * R * K > 16 ? 4 * R * K : 16;
-    int64_t chunks = 2 * slots / bands;   // about two jobs per resident warp
-    if (chunks < 1) chunks = 1;
-    const int64_t max_chunks = ny / min_ly > 1 ? ny / min_ly : 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    p.Ly = (ny + chunks - 1) / chunks;
-    chunks = (ny + p.Ly - 1) / p.Ly;
-    p.bands = bands;
-    p.jobs = bands * chunks;
+    const F2Tiling tl = f2_tiling(nx, ny, G::BW, R * K, (int64_t)P.sm_count * bps * F2_NW, 2, P.tile_rows);
+    p.Ly = tl.Ly;
+    p.bands = tl.bands;
+    p.jobs = tl.bands * tl.chunks;
     int64_t grid = (p.jobs + F2_NW - 1) / F2_NW;
     if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;
     kern<<<(unsigned)grid, F2_NW * 32, smem, st>>>(map, p);
+    return cudaGetLastError();
+}
+
+template <int DT, int R, int PAT, int K>
+cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int passes,
+                          cudaStream_t st) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F2Geo<DT, R, K>;
+    if (!fused2d_multi_ok(P, K) || passes < 1) return cudaErrorNotSupported;
+    F2MpParams<C> p;
+    p.g.n0 = 1;
+    p.g.n1 = P.n[1];
+    p.g.n2 = P.n[2];
+    p.g.bkind = P.bkind;
+    p.g.bval = conv_w<C>(P.bval);
+    p.src0 = src0;
+    p.dst_even = dst_even;
+    p.dst_odd = dst_odd;
+    p.passes = passes;
+    p.status = P.d_status;
+    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
+    const int64_t nx = P.n[2], ny = P.n[1];
+    const bool al = ((uintptr_t)src0 % 16 == 0) && ((uintptr_t)dst_even % 16 == 0) && ((uintptr_t)dst_odd % 16 == 0);
+    p.vec_ok = (nx % G::V == 0) && al;
+    bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && al;
+    CUtensorMap maps[3];
+    memset(maps, 0, sizeof(maps));
+    if (tma) {
+        const int64_t dims[2] = {nx, ny};
+        const uint32_t box[2] = {(uint32_t)G::W, (uint32_t)F2_ROWS};
+        const void *bases[3] = {src0, dst_even, dst_odd};
+        for (int i = 0; i < 3 && tma; ++i) tma = make_tmap(&maps[i], DT, 2, dims, box, bases[i]);
+    }
+    auto kern = tma ? fused2d_mp_kernel<DT, R, PAT, K, PROD_TMA> : fused2d_mp_kernel<DT, R, PAT, K, PROD_REG>;
+    const int smem = tma ? G::SMEM : 0;
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[tma ? 0 : 1]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done[tma ? 0 : 1] = true;
+    }
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F2_NW * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    const int64_t slots = (int64_t)P.sm_count * bps * F2_NW;
+    // about three jobs per resident warp and pass: the next pass's items find
+    // their dependencies finished (with one job per warp the passes would
+    // run in lock step)
+    const F2Tiling tl = f2_tiling(nx, ny, G::BW, R * K, slots, 3, P.tile_rows);
+    if (tl.bands * tl.chunks >= (1ll << 30) / 4 || tl.bands * tl.chunks * (int64_t)passes >= (1ll << 62))
+        return cudaErrorNotSupported;
+    p.bands = (int)tl.bands;
+    p.chunks = (int)tl.chunks;
+    p.Ly = (int)tl.Ly;
+    p.tiles = (int)(tl.bands * tl.chunks);
+    e = ensure_mp_state(P, p.tiles, st);
+    if (e != cudaSuccess) return e;
+    p.ctl = static_cast<MpCtl *>(P.d_mp);
+    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
+    p.cap = (int)P.mp_tiles_cap;
+    p.parity = (int)(P.mp_seq++ & 1u);
+    const int64_t jobs = (int64_t)p.tiles * passes;
+    int64_t grid = (jobs + F2_NW - 1) / F2_NW;
+    if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;
+    kern<<<(unsigned)grid, F2_NW * 32, smem, st>>>(maps[0], maps[1], maps[2], p);
     return cudaGetLastError();
 }
 
@@ -493,6 +717,34 @@ cudaError_t launch_f2_k(const stencil_plan_s &P, const void *src, void *dst, int
         case 7: if constexpr (KM >= 7) return launch_f2_t<DT, R, PAT, 7>(P, src, dst, st); break;
         case 8: if constexpr (KM >= 8) return launch_f2_t<DT, R, PAT, 8>(P, src, dst, st); break;
     }
+    return cudaErrorInvalidValue;
+}
+
+template <int DT, int R, int PAT>
+cudaError_t launch_f2mp_k(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                          cudaStream_t st) {
+    constexpr int KM = f2_kmax<DT>(R);
+    switch (k) {
+        case 1: return launch_f2mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st);
+        case 2: return launch_f2mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st);
+        case 3: if constexpr (KM >= 3) return launch_f2mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
+        case 4: if constexpr (KM >= 4) return launch_f2mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
+        case 5: if constexpr (KM >= 5) return launch_f2mp_t<DT, R, PAT, 5>(P, src0, de, dof, passes, st); break;
+        case 6: if constexpr (KM >= 6) return launch_f2mp_t<DT, R, PAT, 6>(P, src0, de, dof, passes, st); break;
+        case 7: if constexpr (KM >= 7) return launch_f2mp_t<DT, R, PAT, 7>(P, src0, de, dof, passes, st); break;
+        case 8: if constexpr (KM >= 8) return launch_f2mp_t<DT, R, PAT, 8>(P, src0, de, dof, passes, st); break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int DT>
+cudaError_t launch_f2mp_dt(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                           cudaStream_t st) {
+    const bool box = P.pattern == STENCIL_BOX;
+    if (P.r == 1) return box ? launch_f2mp_k<DT, 1, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                             : launch_f2mp_k<DT, 1, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+    if (P.r == 2) return box ? launch_f2mp_k<DT, 2, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                             : launch_f2mp_k<DT, 2, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
     return cudaErrorInvalidValue;
 }
 

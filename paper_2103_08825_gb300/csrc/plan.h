@@ -12,6 +12,7 @@
 
 namespace sg {
 constexpr int kHostMaxPts = 343;
+constexpr size_t kMpCtlBytes = 16;   // one control block of a persistent multi-pass launch
 }
 
 struct stencil_plan_s {
@@ -25,6 +26,7 @@ struct stencil_plan_s {
     double w_eval[sg::kHostMaxPts] = {};
     int eval_to_compact[sg::kHostMaxPts] = {};
     int k = 0;                 // 0 = default
+    int tile_rows = 0;         // 2D fused tile height (0 = default)
     int variant = STENCIL_VARIANT_FUSED;
     bool tuned_plain = false;  // the tuner found the one-step kernel fastest
     int device = 0;
@@ -35,6 +37,11 @@ struct stencil_plan_s {
     int *d_status = nullptr;   // device status word (0 = OK)
     unsigned long long *d_ctr = nullptr;   // two job-ticket counters (same allocation)
     mutable unsigned job_seq = 0;          // launches that used the counters
+    // persistent multi-pass launches: two control blocks, then two per-tile
+    // pass counters; a launch uses one parity and clears the other
+    mutable void *d_mp = nullptr;
+    mutable int64_t mp_tiles_cap = 0;
+    mutable unsigned mp_seq = 0;
     // adjoint workspace
     void *adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
@@ -57,6 +64,14 @@ std::string fused_describe(const stencil_plan_s &P, int k);
 // per-dimension entry points used by launch_fused
 int fused2d_max_k(const stencil_plan_s &P);
 cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
+// `passes` passes of k steps in one persistent launch: pass 0 reads src0, the
+// passes p with (passes - 1 - p) even write dst_even, the others dst_odd.
+// cudaErrorNotSupported when the geometry needs one launch per pass.
+cudaError_t launch_fused2d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                                 int passes, cudaStream_t st);
+bool fused2d_multi_ok(const stencil_plan_s &P, int k);
+// control state of the persistent launches for `tiles` tiles (grown on demand)
+cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t st);
 std::string fused2d_describe(const stencil_plan_s &P, int k);
 int fused3d_max_k(const stencil_plan_s &P);
 cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);

@@ -1,0 +1,174 @@
+"""GPU parity of the persistent multi-pass 2D kernel (all passes of exactly
+k steps in one launch, tiles waiting on their neighbours' previous pass).
+
+Bars: int32 bit-exact against the oracle; FP32 and FP64 bit-identical to the
+one-launch-per-pass fused kernels and to the plain one-step sweep (same
+per-point operation order), and within 1e-5 / 1e-12 normwise of the oracle.
+Grids span many tiles with ragged last bands and chunks, periodic halos that
+reach two tiles, unaligned base pointers (register-load path) and repeated
+runs (the launch alternates two sets of counters).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import BOX, DIRICHLET, PERIODIC, STAR, f32_weights, npoints, uniform01, uniform_u16
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+FUSED, PLAIN, PER_PASS = 0, 1, 2
+
+
+def sgmod():
+    import paper_2103_08825_gb300 as sg
+    sg.load()
+    return sg
+
+
+def run(plan, x, T, k, variant, offset=0):
+    """stencil_run on device tensor x; offset > 0 shifts both grids by that
+    many elements inside larger allocations (unaligned base pointers)."""
+    sg = sgmod()
+    sg.stencil_plan_set_variant(plan, variant)
+    sg.stencil_plan_set_k(plan, k)
+    if offset:
+        xin = torch.empty(x.numel() + offset, dtype=x.dtype, device=DEV)
+        xin[offset:] = x.reshape(-1)
+        xo = torch.empty_like(xin)
+        sg.stencil_run(plan, xin[offset:].view(x.shape), xo[offset:].view(x.shape), T)
+        y = xo[offset:].view(x.shape)
+    else:
+        y = torch.empty_like(x)
+        sg.stencil_run(plan, x, y, T)
+    torch.cuda.synchronize()
+    assert sg.stencil_get_device_status(plan) == 0
+    return y.clone()
+
+
+def normwise(g, o):
+    return float(np.max(np.abs(np.asarray(g, np.float64) - o)) / max(1e-300, np.max(np.abs(o))))
+
+
+# shapes: many bands and chunks with ragged last ones, a single band, few rows
+SHAPES = [(700, 1000), (257, 4100), (2000, 130), (37, 5003), (9, 300)]
+
+
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_int32_bit_exact(pattern, r, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(500 + 10 * r + pattern + 3 * bkind)
+    for shape in SHAPES:
+        w = [float(x) for x in rng.integers(-3, 8, npoints(2, r, pattern))]
+        bval = -777 if bkind == DIRICHLET else 0
+        u0 = uniform_u16(900 + shape[1], shape[0] * shape[1]).reshape(shape)
+        plan = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, bval, sg.STENCIL_I32)
+        x = torch.from_numpy(u0).to(DEV)
+        kmax = sg.stencil_plan_max_k(plan)
+        for k in sorted({1, 2, kmax // 2 or 1, kmax}):
+            for T in (2 * k, 3 * k + 1, 5 * k):
+                ref = oracle.run_int(2, r, pattern, shape, w, bkind, bval, u0, T)
+                got = run(plan, x, T, k, FUSED).cpu().numpy()
+                np.testing.assert_array_equal(got, ref, err_msg=f"{shape} k={k} T={T}")
+                assert sg.stencil_plan_launch_count(plan, T) == 1 + (T % k > 0)
+
+
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_fp32_fp64_identical_to_per_pass_and_oracle(pattern, r, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(600 + 10 * r + pattern + 3 * bkind)
+    for shape in SHAPES[:3]:
+        w = list(rng.uniform(-0.1, 0.4, npoints(2, r, pattern)))
+        bval = 0.25 if bkind == DIRICHLET else 0.0
+        u0 = uniform01(1002, shape[0] * shape[1]).reshape(shape)
+        for dt, tol in ((sg.STENCIL_F32, 1e-5), (sg.STENCIL_F64, 1e-12)):
+            plan = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, bval, dt)
+            if dt == sg.STENCIL_F32:
+                ui = u0.astype(np.float32)
+                ref_w, ref_b, ref_u = f32_weights(w), float(np.float32(bval)), ui.astype(np.float64)
+            else:
+                ui, ref_w, ref_b, ref_u = u0, w, bval, u0
+            x = torch.from_numpy(ui).to(DEV)
+            kmax = sg.stencil_plan_max_k(plan)
+            T = 4 * kmax + 1
+            ref = oracle.run(2, r, pattern, shape, ref_w, bkind, ref_b, ref_u, T)
+            plain = run(plan, x, T, 1, PLAIN)
+            assert normwise(plain.cpu().numpy(), ref) <= tol
+            for k in range(1, kmax + 1):
+                mp = run(plan, x, T, k, FUSED)
+                pp = run(plan, x, T, k, PER_PASS)
+                assert torch.equal(mp, pp), f"{shape} dt={dt} k={k}"
+                assert torch.equal(mp, plain), f"{shape} dt={dt} k={k}"
+
+
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_unaligned_pointers_register_path(bkind):
+    """Base pointers off 16-byte alignment: the register-load producer with
+    L2-coherent loads (data written by other SMs within the launch)."""
+    sg = sgmod()
+    shape, r, pattern = (513, 1031), 1, STAR
+    w = [0.5, 0.125, 0.125, 0.125, 0.125]
+    plan = sg.stencil_plan_create(2, r, shape, pattern, w, bkind, 0.5 if bkind == DIRICHLET else 0.0,
+                                  sg.STENCIL_F32)
+    x = torch.from_numpy(uniform01(77, shape[0] * shape[1]).reshape(shape).astype(np.float32)).to(DEV)
+    for k in (1, 3, 4, 8):
+        T = 6 * k
+        plain = run(plan, x, T, 1, PLAIN)
+        for off in (1, 3):
+            assert torch.equal(run(plan, x, T, k, FUSED, offset=off), plain), f"k={k} offset={off}"
+
+
+def test_repeated_runs_alternate_counters():
+    sg = sgmod()
+    shape = (1500, 1500)
+    w = [1 / 9] * 9
+    plan = sg.stencil_plan_create(2, 1, shape, BOX, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+    x = torch.from_numpy(uniform01(5, shape[0] * shape[1]).reshape(shape).astype(np.float32)).to(DEV)
+    first = run(plan, x, 40, 4, FUSED)
+    for _ in range(4):
+        assert torch.equal(run(plan, x, 40, 4, FUSED), first)
+    # a change of k regrows the counters; per-pass launches in between
+    assert torch.equal(run(plan, x, 40, 8, FUSED), first)
+    assert torch.equal(run(plan, x, 40, 2, PER_PASS), first)
+    assert torch.equal(run(plan, x, 40, 5, FUSED), first)
+
+
+def test_bench_size_many_passes():
+    """2048^2 FP32 2D5P, T = 64: the persistent launch against the oracle."""
+    sg = sgmod()
+    shape, T = (2048, 2048), 64
+    w = [0.5, 0.125, 0.125, 0.125, 0.125]
+    u0 = uniform01(1002, shape[0] * shape[1]).reshape(shape).astype(np.float32)
+    plan = sg.stencil_plan_create(2, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+    x = torch.from_numpy(u0).to(DEV)
+    ref = oracle.run(2, 1, STAR, shape, f32_weights(w), DIRICHLET, 0.0, u0.astype(np.float64), T)
+    for k in (2, 4, 6, 8):
+        got = run(plan, x, T, k, FUSED)
+        assert normwise(got.cpu().numpy(), ref) <= 1e-5
+        assert sg.stencil_plan_launch_count(plan, T) == 1 + (T % k > 0)
+
+
+def test_tile_rows_do_not_change_results():
+    sg = sgmod()
+    shape = (1111, 900)
+    w = [0.5, 0.125, 0.125, 0.125, 0.125]
+    for bkind in (DIRICHLET, PERIODIC):
+        plan = sg.stencil_plan_create(2, 1, shape, STAR, w, bkind, 0.0, sg.STENCIL_F32)
+        x = torch.from_numpy(uniform01(8, shape[0] * shape[1]).reshape(shape).astype(np.float32)).to(DEV)
+        plain = run(plan, x, 24, 1, PLAIN)
+        for rows in (1, 16, 17, 50, 333, 5000):
+            sg.stencil_plan_set_tile_rows(plan, rows)
+            assert sg.stencil_plan_get_tile_rows(plan) == rows
+            for k in (2, 4, 8):
+                assert torch.equal(run(plan, x, 24, k, FUSED), plain), f"rows={rows} k={k}"
+                assert torch.equal(run(plan, x, 24, k, PER_PASS), plain), f"rows={rows} k={k}"
+        sg.stencil_plan_set_tile_rows(plan, 0)
+        k, ms = sg.stencil_plan_tune(plan, 24)
+        assert sg.stencil_plan_get_tile_rows(plan) in (0, 32, 48, 64, 96, 128, 192)
+        assert torch.equal(run(plan, x, 24, max(k, 1), PLAIN if k == 0 else FUSED), plain)

@@ -217,6 +217,11 @@ def test_zero_steps_and_ragged_pass_counts():
     base = gpu_run(plan, u0, 11, variant=1).cpu().numpy()
     for k in kvalues(plan):
         np.testing.assert_array_equal(gpu_run(plan, u0, 11, k=k).cpu().numpy(), base)
+        # 2D: the passes of exactly k steps share one persistent launch
+        full = 11 // k
+        assert sg.stencil_plan_launch_count(plan, 11) == (1 + (11 % k > 0) if full >= 2 else -(-11 // k))
+        np.testing.assert_array_equal(gpu_run(plan, u0, 11, k=k, variant=sg.STENCIL_VARIANT_FUSED_PER_PASS)
+                                      .cpu().numpy(), base)
         assert sg.stencil_plan_launch_count(plan, 11) == -(-11 // k)
 
 
