@@ -48,9 +48,13 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture, keyed by workload, k and a hash of the kernel sources it was
-# measured on; reported as null once those sources change.
-NCU_TRAFFIC = {}
+# capture, keyed by workload, k, tile height and a hash of the kernel sources
+# it was measured on; reported as null once those sources change.
+NCU_TRAFFIC = {
+    # 2D 5-point 8192^2 FP32, T = 64, k = 4, 64-row tiles: all 16 passes in one
+    # launch, read 5.039748 GB + write 4.250728 GB
+    "2d5p:k4:rows64:3d781d4d2d36bfd6": 9290476000,
+}
 
 KERNEL_SOURCES = ["paper_2103_08825_gb300/csrc/k_fused2d.cuh", "paper_2103_08825_gb300/csrc/common.cuh"]
 
@@ -338,6 +342,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d5p", choices=sorted(WORKLOADS) + ["batch", "adjoint"])
     ap.add_argument("--k", type=int, default=0, help="fusion depth (0 = autotune)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="2D tile height with --k (0 = the plan's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=0, help="steps for the plain sweep (0 = steps/4)")
     args = ap.parse_args()
@@ -384,10 +389,12 @@ def main():
 
     if args.k > 0:
         sg.stencil_plan_set_k(plan, args.k)
+        sg.stencil_plan_set_tile_rows(plan, args.tile_rows)
         tuned = None
     else:
         tuned = sg.stencil_plan_tune(plan, p.T)
     k = sg.stencil_plan_get_k(plan)
+    variant = sg.stencil_plan_get_variant(plan)
     launches = sg.stencil_plan_launch_count(plan, p.T)
 
     def barrier():
@@ -443,10 +450,8 @@ def main():
         ms_k1 = timed(fused_step, plain_steps, 3) / plain_steps
         one_step_fused = upd_step / (ms_k1 * 1e-3) / 1e9
     # restore the timed configuration
-    if tuned is not None and tuned[0] == 0:
-        sg.stencil_plan_set_variant(plan, sg.STENCIL_VARIANT_PLAIN)
-    else:
-        sg.stencil_plan_set_variant(plan, sg.STENCIL_VARIANT_FUSED)
+    sg.stencil_plan_set_variant(plan, variant)
+    if variant != sg.STENCIL_VARIANT_PLAIN:
         sg.stencil_plan_set_k(plan, k)
 
     # roofline of the fused sweep: algorithmic bytes (one read and one write
@@ -454,11 +459,11 @@ def main():
     # persistent kernel one launch carries every pass of exactly k steps, so
     # when T is a multiple of k the step is that single launch.
     peak, peak_kind = measured_peaks()
-    fused_now = not (tuned is not None and tuned[0] == 0)
+    fused_now = variant != sg.STENCIL_VARIANT_PLAIN
     passes = -(-p.T // k) if fused_now else p.T
     bytes_step = 2.0 * p.npts * esize * passes
     achieved = bytes_step / (ms_step * 1e-3) / 1e9
-    key = f"{args.workload}:k{k}:{kernel_hash()}"
+    key = f"{args.workload}:k{k}:rows{sg.stencil_plan_get_tile_rows(plan)}:{kernel_hash()}"
     traffic = NCU_TRAFFIC.get(key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": sg.stencil_plan_describe(plan),
@@ -517,7 +522,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtn, "data": "synthetic (seeded uniform[0,1), fixed boundary)",
             "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T, "k": k,
-                       "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan)}
+                       "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan),
+                                 "launch": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass"}[variant]}
                        if tuned else None,
                        "l2": f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

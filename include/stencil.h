@@ -70,8 +70,9 @@ typedef enum { STENCIL_STAR = 0, STENCIL_BOX = 1 } stencil_pattern_t;
 typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_kind_t;
 
 /* Which kernels stencil_run uses.  FUSED: k steps per pass (the default);
- * for 2D grids the passes of exactly k steps run as one persistent launch
- * whose tiles wait on their neighbours' completion of the previous pass.
+ * for 2D and 3D grids the passes of exactly k steps run as one persistent
+ * launch whose tiles wait on their neighbours' completion of the previous
+ * pass.
  * PLAIN: one step per launch, each thread reading its own neighbours -- the
  * one-step-per-launch sweep the fused path is measured against.
  * FUSED_PER_PASS: the fused kernels with one launch per pass. */
@@ -114,29 +115,36 @@ stencil_status_t stencil_plan_get_k(stencil_plan_t plan, int32_t *k);
 /* Largest k the fused kernels accept for this plan. */
 stencil_status_t stencil_plan_max_k(stencil_plan_t plan, int32_t *kmax);
 
-/* Select FUSED (default), PLAIN or FUSED_PER_PASS kernels for stencil_run. */
+/* Select FUSED (default), PLAIN or FUSED_PER_PASS kernels for stencil_run;
+ * get returns the kernels stencil_run uses now (after stencil_plan_tune, the
+ * tuner's choice). */
 stencil_status_t stencil_plan_set_variant(stencil_plan_t plan, int32_t variant);
+stencil_status_t stencil_plan_get_variant(stencil_plan_t plan, int32_t *variant);
 
-/* Tile height of the fused 2D kernels: the rows (outermost dimension) one
- * warp job advances; at least max(4 r k, 16) and at most the grid's rows
- * are used.  0 selects the default (about two jobs per resident warp per
- * pass).  1D and 3D plans keep the value and ignore it. */
+/* Tile length of the fused kernels along the outermost dimension: in 2D the
+ * rows one warp job advances (at least max(4 r k, 16)), in 3D the z planes
+ * one CTA job advances (at least max(4 r k, 8)); at most the grid's extent
+ * is used.  0 selects the default (about two to three jobs per resident warp
+ * or CTA per pass).  1D plans keep the value and ignore it. */
 stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t plan, int32_t rows);
 stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t plan, int32_t *rows);
 
-/* Autotune the fusion depth and (2D) the tile height: times stencil_run for
- * the one-step kernel and for every supported k -- in 2D with each of a few
- * tile heights -- on plan-owned buffers holding zeros, with CUDA events on
- * `stream`, and keeps the fastest (for tiny or FP64-pipe-bound grids the
- * one-step kernel can win).  Synchronises `stream`.  `T` is the step count to
- * tune for; best_k (may be NULL) receives the chosen k, or 0 when the
- * one-step kernel won; best_ms (may be NULL) its time; the chosen tile
- * height is read with stencil_plan_get_tile_rows.  stencil_plan_set_k and
- * stencil_plan_set_variant discard the choice of kernel. */
+/* Autotune the fusion depth, the launch form and (2D, 3D) the tile length:
+ * times stencil_run for the one-step kernel and, for every supported k, the
+ * fused kernels with one launch per pass and -- in 2D and 3D -- the
+ * persistent multi-pass launch with each of a few tile lengths, on
+ * plan-owned buffers holding zeros, with CUDA events on `stream`, and keeps
+ * the fastest (for tiny or FP64-pipe-bound grids the one-step kernel can
+ * win).  Synchronises `stream`.  `T` is the step count to tune for; best_k
+ * (may be NULL) receives the chosen k, or 0 when the one-step kernel won;
+ * best_ms (may be NULL) its time; the chosen launch form and tile length are
+ * read with stencil_plan_get_variant and stencil_plan_get_tile_rows.
+ * stencil_plan_set_k and stencil_plan_set_variant discard the choice of
+ * kernel. */
 stencil_status_t stencil_plan_tune(stencil_plan_t plan, int64_t T, void *stream, int32_t *best_k, double *best_ms);
 
 /* Number of kernel launches stencil_run makes for T steps with the current
- * variant and k: T plain steps, ceil(T/k) fused passes, or for the 2D
+ * variant and k: T plain steps, ceil(T/k) fused passes, or for the 2D/3D
  * persistent form one launch plus one for a last pass of T mod k steps. */
 stencil_status_t stencil_plan_launch_count(stencil_plan_t plan, int64_t T, int64_t *launches);
 

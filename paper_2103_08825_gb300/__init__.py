@@ -28,7 +28,8 @@ STENCIL_REDUCE_SUM, STENCIL_REDUCE_SUMSQ, STENCIL_REDUCE_HALF_SQDIST = 0, 1, 2
 # Every symbol include/stencil.h declares (checked by the CPU test suite).
 EXPORTS = [
     "stencil_plan_create", "stencil_plan_destroy", "stencil_plan_set_k", "stencil_plan_get_k",
-    "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_set_tile_rows", "stencil_plan_get_tile_rows",
+    "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_get_variant", "stencil_plan_set_tile_rows",
+    "stencil_plan_get_tile_rows",
     "stencil_plan_tune", "stencil_plan_launch_count",
     "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_batch_create",
     "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status",
@@ -74,6 +75,7 @@ def load(path: str | None = None):
         "stencil_plan_get_k": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_max_k": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_set_variant": (st, [vp, i32]),
+        "stencil_plan_get_variant": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_set_tile_rows": (st, [vp, i32]),
         "stencil_plan_get_tile_rows": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_tune": (st, [vp, i64, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
@@ -184,6 +186,12 @@ def stencil_plan_max_k(plan: Plan) -> int:
 
 def stencil_plan_set_variant(plan: Plan, variant: int):
     _check(load().stencil_plan_set_variant(plan.handle, int(variant)), "stencil_plan_set_variant")
+
+
+def stencil_plan_get_variant(plan: Plan) -> int:
+    v = ctypes.c_int32()
+    _check(load().stencil_plan_get_variant(plan.handle, ctypes.byref(v)), "stencil_plan_get_variant")
+    return v.value
 
 
 def stencil_plan_set_tile_rows(plan: Plan, rows: int):

@@ -172,7 +172,7 @@ static bool uses_fused(const stencil_plan_s *P) {
 // passes of exactly k steps that stencil_run gives one persistent launch
 // (0: one launch per pass)
 static int64_t multi_passes(const stencil_plan_s *P, int k, int64_t T) {
-    if (P->variant != STENCIL_VARIANT_FUSED || P->dim != 2 || !fused2d_multi_ok(*P, k)) return 0;
+    if (P->variant != STENCIL_VARIANT_FUSED || !fused_multi_ok(*P, k)) return 0;
     const int64_t full = T / k;
     return full >= 2 && full <= (1 << 30) ? full : 0;
 }
@@ -327,6 +327,12 @@ stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
     return STENCIL_OK;
 }
 
+stencil_status_t stencil_plan_get_variant(stencil_plan_t P, int32_t *variant) {
+    if (!P || !variant) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *variant = P->tuned_plain ? STENCIL_VARIANT_PLAIN : P->variant;
+    return STENCIL_OK;
+}
+
 stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t P, int32_t rows) {
     if (!P || rows < 0) { set_error("invalid plan or tile height"); return STENCIL_ERR_INVALID_ARG; }
     P->tile_rows = rows;
@@ -387,7 +393,7 @@ stencil_status_t stencil_run(stencil_plan_t P, const void *u_in, void *u_out, in
         // pass mp-1 of the loop below would
         void *de = ((passes - mp) % 2 == 0) ? u_out : P->ws;
         void *dof = de == u_out ? P->ws : u_out;
-        cudaError_t e = launch_fused2d_multi(*P, u_in, de, dof, k, (int)mp, st);
+        cudaError_t e = launch_fused_multi(*P, u_in, de, dof, k, (int)mp, st);
         if (e == cudaSuccess) {
             p0 = mp;
             src = de;
@@ -425,7 +431,7 @@ stencil_status_t stencil_run_host(stencil_plan_t P, const void *h_in, void *h_ou
 stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, int32_t *best_k, double *best_ms) {
     if (!P || T < 1) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
     const int km = fused_max_k(*P);
-    if (km <= 0 || P->variant != STENCIL_VARIANT_FUSED) {
+    if (km <= 0 || P->variant == STENCIL_VARIANT_PLAIN) {
         if (best_k) *best_k = 1;
         if (best_ms) *best_ms = -1.0;
         return STENCIL_OK;
@@ -439,8 +445,8 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved = P->k, saved_rows = P->tile_rows;
-    int bk = 1, brows = saved_rows;
+    const int saved = P->k, saved_rows = P->tile_rows, saved_variant = P->variant;
+    int bk = 1, brows = saved_rows, bvariant = saved_variant;
     float bms = 1e30f;
     bool best_plain = false;
     // tile heights tried in 2D: the default and a few fixed heights below
@@ -449,12 +455,27 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     if (P->dim == 2)
         for (int r : {32, 48, 64, 96, 128, 192})
             if (r < P->n[1]) rows_c.push_back(r);
-    // candidates: the one-step kernel (k = 0 here), then every fused depth
+    if (P->dim == 3)
+        for (int r : {16, 32, 48, 64})
+            if (r < P->n[0]) rows_c.push_back(r);
+    // candidates: the one-step kernel (k = 0 here), then every fused depth,
+    // one launch per pass (default tiles) and -- where the grid allows it --
+    // the persistent multi-pass launch with each tile length
+    struct Cand { int variant, rows; };
     for (int k = 0; k <= km && s == STENCIL_OK; ++k) {
-        for (size_t ri = 0; ri < (k == 0 ? 1 : rows_c.size()); ++ri) {
+        std::vector<Cand> cands;
+        if (k == 0) {
+            cands.push_back({STENCIL_VARIANT_FUSED, 0});
+        } else {
+            cands.push_back({STENCIL_VARIANT_FUSED_PER_PASS, 0});
+            if (fused_multi_ok(*P, k))
+                for (int r : rows_c) cands.push_back({STENCIL_VARIANT_FUSED, r});
+        }
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
             P->tuned_plain = (k == 0);
             P->k = k == 0 ? 1 : k;
-            P->tile_rows = rows_c[ri];
+            P->variant = cands[ci].variant;
+            P->tile_rows = cands[ci].rows;
             s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
             if (s != STENCIL_OK) break;
             float best_rep = 1e30f;
@@ -474,15 +495,23 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
                 bms = best_rep;
                 bk = k == 0 ? 1 : k;
                 best_plain = (k == 0);
-                brows = rows_c[ri];
+                brows = cands[ci].rows;
+                bvariant = k == 0 ? saved_variant : cands[ci].variant;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (s != STENCIL_OK) { P->k = saved; P->tile_rows = saved_rows; P->tuned_plain = false; return s; }
+    if (s != STENCIL_OK) {
+        P->k = saved;
+        P->tile_rows = saved_rows;
+        P->variant = saved_variant;
+        P->tuned_plain = false;
+        return s;
+    }
     P->k = bk;
     P->tile_rows = best_plain ? saved_rows : brows;
+    P->variant = bvariant;
     P->tuned_plain = best_plain;
     if (best_k) *best_k = best_plain ? 0 : bk;
     if (best_ms) *best_ms = bms;

@@ -199,6 +199,13 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
     return v;
 }
 
+// *ctr += v with release semantics at GPU scope: this thread's earlier
+// accesses (and those it has observed, e.g. through __syncwarp) are visible
+// to any thread that acquires the new value
+__device__ __forceinline__ void red_release_add(int *ctr, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(ctr), "r"(v) : "memory");
+}
+
 // orders this thread's generic-proxy global accesses with its async-proxy
 // (TMA) ones: taken after acquiring data that other CTAs stored and before
 // reading it by TMA, and after storing data that other CTAs will read by TMA

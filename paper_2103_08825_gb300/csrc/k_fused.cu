@@ -81,7 +81,9 @@ std::string fused2d_describe(const stencil_plan_s &P, int k) {
            (P.tile_rows > 0 ? std::to_string(P.tile_rows) : std::string("default")) + ")";
 }
 
-#define SG_DECL_F3(DT) cudaError_t launch_f3_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+#define SG_DECL_F3(DT)                                                                              \
+    cudaError_t launch_f3_##DT(const stencil_plan_s &, const void *, void *, int, cudaStream_t);   \
+    cudaError_t launch_f3mp_##DT(const stencil_plan_s &, const void *, void *, void *, int, int, cudaStream_t);
 SG_DECL_F3(F32)
 SG_DECL_F3(F64)
 SG_DECL_F3(BF16)
@@ -108,8 +110,45 @@ cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, 
     return cudaErrorInvalidValue;
 }
 
+// As fused2d_multi_ok, for the 3D window (x halo rounded to the TMA
+// alignment, y and z halos rK).
+bool fused3d_multi_ok(const stencil_plan_s &P, int k) {
+    if (P.dim != 3 || k < 1 || k > fused3d_max_k(P)) return false;
+    const int v = P.dtype == STENCIL_F64 ? 2 : 4;
+    const int al = std::max(16 / (int)dtype_size(P.dtype), v);
+    const int64_t h = (P.r * k + al - 1) / al * al, rk = (int64_t)P.r * k;
+    const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
+    if (nx + 512 >= (1ll << 30) || ny + 512 >= (1ll << 30) || nz + 4 * rk + 64 >= (1ll << 30)) return false;
+    if (P.bkind == STENCIL_PERIODIC && (h > nx || rk > ny || rk > nz)) return false;
+    return true;
+}
+
+cudaError_t launch_fused3d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                                 int passes, cudaStream_t st) {
+    switch (P.dtype) {
+        case STENCIL_F32: return launch_f3mp_F32(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_F64: return launch_f3mp_F64(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_BF16: return launch_f3mp_BF16(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_F16: return launch_f3mp_F16(P, src0, dst_even, dst_odd, k, passes, st);
+        case STENCIL_I32: return launch_f3mp_I32(P, src0, dst_even, dst_odd, k, passes, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool fused_multi_ok(const stencil_plan_s &P, int k) {
+    return P.dim == 2 ? fused2d_multi_ok(P, k) : P.dim == 3 ? fused3d_multi_ok(P, k) : false;
+}
+
+cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                               int passes, cudaStream_t st) {
+    if (P.dim == 2) return launch_fused2d_multi(P, src0, dst_even, dst_odd, k, passes, st);
+    if (P.dim == 3) return launch_fused3d_multi(P, src0, dst_even, dst_odd, k, passes, st);
+    return cudaErrorNotSupported;
+}
+
 std::string fused3d_describe(const stencil_plan_s &P, int k) {
-    return "fused3d(z-streamed planes, 16 warps x 2 rows, k=" + std::to_string(k) + ")";
+    return "fused3d(z-streamed planes, 16 warps x 2 rows, k=" + std::to_string(k) + ", planes per job=" +
+           (P.tile_rows > 0 ? std::to_string(P.tile_rows) : std::string("default")) + ")";
 }
 
 int fused_max_k(const stencil_plan_s &P) {

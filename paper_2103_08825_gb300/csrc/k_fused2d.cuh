@@ -489,16 +489,19 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     const int jobs = p.bands * p.chunks;
     const unsigned long long items = (unsigned long long)jobs * (unsigned)p.passes;
     uint32_t gst = 0;
+    // the next ticket and the abort flag are fetched one job ahead, so that
+    // their latency overlaps the current job
+    unsigned long long t_next = 0;
+    int ab_next = 0;
+    if (lane == 0) t_next = atomicAdd(&ctl->ticket, 1ull);
     for (;;) {
-        unsigned long long t = 0;
-        int ab = 0;
-        if (lane == 0) {
-            t = atomicAdd(&ctl->ticket, 1ull);
-            ab = ld_relaxed(&ctl->abort);
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
-        ab = __shfl_sync(0xffffffffu, ab, 0);
+        const unsigned long long t = __shfl_sync(0xffffffffu, t_next, 0);
+        const int ab = __shfl_sync(0xffffffffu, ab_next, 0);
         if (t >= items || ab) break;
+        if (lane == 0) {
+            t_next = atomicAdd(&ctl->ticket, 1ull);
+            ab_next = ld_relaxed(&ctl->abort);
+        }
         const int pass = (int)(t / (unsigned)jobs), j = (int)(t % (unsigned)jobs);
         const int chunk = j / p.bands, band = j - chunk * p.bands;
         const int yo0 = chunk * p.Ly;
@@ -521,8 +524,12 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
                 }
                 return;
             }
-            __threadfence();
-            if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
+            // every lane's acquire precedes every lane's reads; TMA reads
+            // (async proxy) also need the proxy fence
+            __syncwarp();
+            if constexpr (PROD == PROD_TMA) {
+                if (lane == 0) fence_proxy_async_global();
+            }
         }
         const bool from_even = ((p.passes - pass) & 1) == 0;   // pass - 1 wrote dst_even
         const S *src = static_cast<const S *>(pass == 0 ? p.src0 : from_even ? p.dst_even : p.dst_odd);
@@ -542,12 +549,11 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
             }
             return;
         }
-        // publish: this warp's stores, then the tile's pass count
+        // publish: every lane's stores, then (release) the tile's pass count
         __syncwarp();
         if (lane == 0) {
             if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
-            __threadfence();
-            atomicAdd(&done[j], 1);
+            red_release_add(&done[j], 1);
         }
     }
 }

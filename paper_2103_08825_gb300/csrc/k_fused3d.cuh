@@ -70,6 +70,22 @@ template <typename C> struct F3Params {
     C w[125];               // evaluation order; up to the r = 2 box
 };
 
+template <typename C> struct F3MpParams {
+    GridGeom<C> g;          // n0 = nz, n1 = ny, n2 = nx
+    const void *src0;       // input of pass 0
+    void *dst_even;         // output of the passes p with (passes - 1 - p) even (includes the last)
+    void *dst_odd;
+    int passes;
+    int tiles_x, tiles_y, chunks, Lz;
+    int vec_ok;
+    int *status;
+    MpCtl *ctl;             // [2]; this launch uses ctl[parity], clears ctl[parity ^ 1]
+    int *done;              // [2][cap]: passes each tile has finished
+    int tiles, cap;
+    int parity;
+    C w[125];
+};
+
 // V arithmetic values (16 or 32 bytes) to / from shared memory, 16-byte accesses
 template <typename C, int V> __device__ __forceinline__ void st_shared_vec(C *p, const C *v) {
     static_assert((V * sizeof(C)) % 16 == 0, "16-byte units");
@@ -273,6 +289,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
             // ---- C: K levels
 #pragma unroll
             for (int s = 0; s < K; ++s) {
+                C emit[RY][V];
                 // x-extended rows (star: only the own rows need x-neighbours)
                 C ext[NR][V + 2 * R];
 #pragma unroll
@@ -289,7 +306,6 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     }
                 }
                 const int s0 = ph % NS;
-                C emit[RY][V];
                 // complete plane J - R: o_z = +R terms
 #pragma unroll
                 for (int j = 0; j < RY; ++j)
@@ -489,6 +505,145 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     }
 }
 
+// All `passes` passes of K steps in one persistent launch (3D form of
+// fused2d_mp_kernel): CTAs take (pass, tile) items from one ticket,
+// pass-major and z-major within a pass; an item of pass p first waits until
+// every tile whose output meets its input window (up to 3 x 3 x 3 tiles, one
+// thread each) has finished pass p - 1; completion is published with release
+// semantics after the CTA's stores.  Waits are bounded (about one second); a
+// wait that gives up raises the abort flag and records STENCIL_ERR_TIMEOUT.
+template <int DT, int R, int PAT, int K, int PROD>
+__global__ void __launch_bounds__(F3_THREADS, 1)
+    fused3d_mp_kernel(const __grid_constant__ CUtensorMap tm_src0, const __grid_constant__ CUtensorMap tm_even,
+                      const __grid_constant__ CUtensorMap tm_odd,
+                      const __grid_constant__ F3MpParams<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F3Geo<DT, R, K>;
+    using Sh = Shape<3, R, PAT>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    S *stages = reinterpret_cast<S *>(smem);
+    C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::STAGE_BYTES + G::XBUF_BYTES);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = (int)p.g.n2, ny = (int)p.g.n1, nz = (int)p.g.n0;
+    const bool dir = p.g.bkind == STENCIL_DIRICHLET;
+    if constexpr (PROD == PROD3_TMA) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < F3_STAGES; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+            prefetch_tmap(&tm_src0);
+            prefetch_tmap(&tm_even);
+            prefetch_tmap(&tm_odd);
+        }
+    }
+    // clear the other parity's counters for the next launch (stream-ordered)
+    {
+        int *other = p.done + (size_t)(p.parity ^ 1) * p.cap;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.cap; i += gridDim.x * blockDim.x) other[i] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            p.ctl[p.parity ^ 1].ticket = 0ull;
+            p.ctl[p.parity ^ 1].abort = 0;
+        }
+    }
+    __syncthreads();
+    MpCtl *ctl = p.ctl + p.parity;
+    int *done = p.done + (size_t)p.parity * p.cap;
+    C wr[Sh::npts];
+#pragma unroll
+    for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
+    uint32_t gst = 0;
+    int xpar = 0;
+    const int txy = p.tiles_x * p.tiles_y;
+    const int jobs = txy * p.chunks;
+    const unsigned long long items = (unsigned long long)jobs * (unsigned)p.passes;
+    __shared__ unsigned long long s_ticket;
+    __shared__ int s_abort;
+    // the next ticket and the abort flag are fetched one job ahead
+    unsigned long long t_next = 0;
+    int ab_next = 0;
+    if (threadIdx.x == 0) t_next = atomicAdd(&ctl->ticket, 1ull);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_ticket = t_next;
+            s_abort = ab_next;
+        }
+        __syncthreads();
+        const unsigned long long t = s_ticket;
+        const int ab = s_abort;
+        __syncthreads();
+        if (t >= items || ab) break;
+        if (threadIdx.x == 0) {
+            t_next = atomicAdd(&ctl->ticket, 1ull);
+            ab_next = ld_relaxed(&ctl->abort);
+        }
+        const int pass = (int)(t / (unsigned)jobs), j = (int)(t % (unsigned)jobs);
+        const int cz = j / txy, rest = j - cz * txy;
+        const int ty = rest / p.tiles_x, tx = rest - ty * p.tiles_x;
+        const int xo0 = tx * G::BW, yo0 = ty * G::BY;
+        const int zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
+        if (pass > 0) {
+            const int xe = xo0 + G::BW < nx ? xo0 + G::BW : nx;
+            const int ye = yo0 + G::BY < ny ? yo0 + G::BY : ny;
+            const TileSpan sx = tile_span(xo0 - G::H, xe + G::H, nx, G::BW, !dir);
+            const TileSpan sy = tile_span(yo0 - G::HY, ye + G::HY, ny, G::BY, !dir);
+            const TileSpan sz = tile_span(zo0 - R * K, zo1 + R * K, nz, p.Lz, !dir);
+            const int cx = sx.count(), cxy = cx * sy.count(), nd = cxy * sz.count();
+            bool ok = true;
+            for (int e = threadIdx.x; e < nd; e += F3_THREADS) {
+                const int ex = sx.at(e % cx), ey = sy.at((e % cxy) / cx), ez = sz.at(e / cxy);
+                ok = ok && wait_counter(&done[(ez * p.tiles_y + ey) * p.tiles_x + ex], pass, &ctl->abort);
+            }
+            // the barrier orders every thread's acquire before every thread's reads
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(&ctl->abort, 1);
+                    record_status(p.status, kStatusTimeout);
+                }
+                return;
+            }
+            if constexpr (PROD == PROD3_TMA) {
+                if (threadIdx.x == 0) fence_proxy_async_global();
+            }
+        }
+        const bool from_even = ((p.passes - pass) & 1) == 0;   // pass - 1 wrote dst_even
+        const S *src = static_cast<const S *>(pass == 0 ? p.src0 : from_even ? p.dst_even : p.dst_odd);
+        const CUtensorMap *tm = pass == 0 ? &tm_src0 : from_even ? &tm_even : &tm_odd;
+        S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
+        const bool interior = !dir || (xo0 - G::H >= 0 && xo0 - G::H + G::W <= nx && yo0 - G::HY >= 0 &&
+                                       yo0 - G::HY + F3_WY <= ny && zo0 - R * K >= 0 && zo1 + R * K <= nz);
+        const bool ok = interior
+            ? fused3d_job<DT, R, PAT, K, PROD, false>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1,
+                                                     p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane, warp)
+            : fused3d_job<DT, R, PAT, K, PROD, true>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1,
+                                                    p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane, warp);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicExch(&ctl->abort, 1);
+                record_status(p.status, kStatusTimeout);
+            }
+            return;
+        }
+        // fused3d_job ends with a barrier after the CTA's last stores: publish
+        if (threadIdx.x == 0) {
+            if constexpr (PROD == PROD3_TMA) fence_proxy_async_global();
+            red_release_add(&done[j], 1);
+        }
+    }
+}
+
+// z ranges: `lz` planes if set, else about three jobs per resident CTA;
+// each range at least max(4 rK, 8) planes long
+inline int64_t f3_lz(int64_t nz, int64_t tiles, int64_t slots, int rk, int lz) {
+    const int64_t min_lz = 4 * rk > 8 ? 4 * rk : 8;
+    if (lz > 0) return lz > min_lz ? (lz < nz ? lz : nz) : (min_lz < nz ? min_lz : nz);
+    int64_t best_c = (3 * slots + tiles - 1) / tiles;
+    if (best_c < 1) best_c = 1;
+    const int64_t max_c = nz / min_lz > 1 ? nz / min_lz : 1;
+    if (best_c > max_c) best_c = max_c;
+    return (nz + best_c - 1) / best_c;
+}
+
 template <int DT, int R, int PAT, int K>
 cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
     using S = typename Traits<DT>::S;
@@ -535,14 +690,8 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.tiles_y = (ny + G::BY - 1) / G::BY;
     const int64_t tiles = p.tiles_x * p.tiles_y;
     const int64_t slots = (int64_t)P.sm_count * bps;
-    // z ranges: about three jobs per resident CTA (taken dynamically), each
-    // range at least 4 rK planes long
-    const int64_t min_lz = 4 * R * K > 8 ? 4 * R * K : 8;
-    int64_t best_c = (3 * slots + tiles - 1) / tiles;
-    if (best_c < 1) best_c = 1;
-    const int64_t max_c = nz / min_lz > 1 ? nz / min_lz : 1;
-    if (best_c > max_c) best_c = max_c;
-    p.Lz = (nz + best_c - 1) / best_c;
+    // z ranges: about three jobs per resident CTA (taken dynamically)
+    p.Lz = f3_lz(nz, tiles, slots, R * K, P.tile_rows);
     const int64_t chunks = (nz + p.Lz - 1) / p.Lz;
     p.jobs = tiles * chunks;
     int64_t grid = p.jobs < slots ? p.jobs : slots;
@@ -550,7 +699,97 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     return cudaGetLastError();
 }
 
+template <int DT, int R, int PAT, int K>
+cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int passes,
+                          cudaStream_t st) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using G = F3Geo<DT, R, K>;
+    if (!fused3d_multi_ok(P, K) || passes < 1) return cudaErrorNotSupported;
+    F3MpParams<C> p;
+    p.g.n0 = P.n[0];
+    p.g.n1 = P.n[1];
+    p.g.n2 = P.n[2];
+    p.g.bkind = P.bkind;
+    p.g.bval = conv_w<C>(P.bval);
+    p.src0 = src0;
+    p.dst_even = dst_even;
+    p.dst_odd = dst_odd;
+    p.passes = passes;
+    p.status = P.d_status;
+    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
+    const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
+    const bool al = ((uintptr_t)src0 % 16 == 0) && ((uintptr_t)dst_even % 16 == 0) && ((uintptr_t)dst_odd % 16 == 0);
+    p.vec_ok = (nx % G::V == 0) && al;
+    bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && al;
+    CUtensorMap maps[3];
+    memset(maps, 0, sizeof(maps));
+    if (tma) {
+        const int64_t dims[3] = {nx, ny, nz};
+        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)F3_WY, 1u};
+        const void *bases[3] = {src0, dst_even, dst_odd};
+        for (int i = 0; i < 3 && tma; ++i) tma = make_tmap(&maps[i], DT, 3, dims, box, bases[i]);
+    }
+    if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
+    auto kern = tma ? fused3d_mp_kernel<DT, R, PAT, K, PROD3_TMA> : fused3d_mp_kernel<DT, R, PAT, K, PROD3_CPASYNC>;
+    const int smem = G::SMEM;
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[tma ? 0 : 1]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done[tma ? 0 : 1] = true;
+    }
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F3_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    const int64_t tiles_x = (nx + G::BW - 1) / G::BW, tiles_y = (ny + G::BY - 1) / G::BY;
+    const int64_t slots = (int64_t)P.sm_count * bps;
+    const int64_t lz = f3_lz(nz, tiles_x * tiles_y, slots, R * K, P.tile_rows);
+    const int64_t chunks = (nz + lz - 1) / lz;
+    const int64_t tiles = tiles_x * tiles_y * chunks;
+    if (tiles >= (1ll << 28)) return cudaErrorNotSupported;
+    p.tiles_x = (int)tiles_x;
+    p.tiles_y = (int)tiles_y;
+    p.chunks = (int)chunks;
+    p.Lz = (int)lz;
+    p.tiles = (int)tiles;
+    e = ensure_mp_state(P, tiles, st);
+    if (e != cudaSuccess) return e;
+    p.ctl = static_cast<MpCtl *>(P.d_mp);
+    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
+    p.cap = (int)P.mp_tiles_cap;
+    p.parity = (int)(P.mp_seq++ & 1u);
+    const int64_t jobs = tiles * passes;
+    const int64_t grid = jobs < slots ? jobs : slots;
+    kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(maps[0], maps[1], maps[2], p);
+    return cudaGetLastError();
+}
+
 template <int DT> constexpr int f3_kmax(int r) { return r == 1 ? 4 : 2; }
+
+template <int DT, int R, int PAT>
+cudaError_t launch_f3mp_k(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                          cudaStream_t st) {
+    switch (k) {
+        case 1: return launch_f3mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st);
+        case 2: return launch_f3mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st);
+        case 3: if constexpr (R == 1) return launch_f3mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
+        case 4: if constexpr (R == 1) return launch_f3mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int DT>
+cudaError_t launch_f3mp_dt(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                           cudaStream_t st) {
+    const bool box = P.pattern == STENCIL_BOX;
+    if (P.r == 1) return box ? launch_f3mp_k<DT, 1, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                             : launch_f3mp_k<DT, 1, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+    if (P.r == 2) return box ? launch_f3mp_k<DT, 2, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                             : launch_f3mp_k<DT, 2, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+    return cudaErrorInvalidValue;
+}
 
 template <int DT, int R, int PAT>
 cudaError_t launch_f3_k(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {

@@ -70,6 +70,13 @@ cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, 
 cudaError_t launch_fused2d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
                                  int passes, cudaStream_t st);
 bool fused2d_multi_ok(const stencil_plan_s &P, int k);
+bool fused3d_multi_ok(const stencil_plan_s &P, int k);
+cudaError_t launch_fused3d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                                 int passes, cudaStream_t st);
+// the persistent multi-pass form for the plan's dimension (2D or 3D)
+bool fused_multi_ok(const stencil_plan_s &P, int k);
+cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                               int passes, cudaStream_t st);
 // control state of the persistent launches for `tiles` tiles (grown on demand)
 cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t st);
 std::string fused2d_describe(const stencil_plan_s &P, int k);

@@ -171,4 +171,75 @@ def test_tile_rows_do_not_change_results():
         sg.stencil_plan_set_tile_rows(plan, 0)
         k, ms = sg.stencil_plan_tune(plan, 24)
         assert sg.stencil_plan_get_tile_rows(plan) in (0, 32, 48, 64, 96, 128, 192)
-        assert torch.equal(run(plan, x, 24, max(k, 1), PLAIN if k == 0 else FUSED), plain)
+        v = sg.stencil_plan_get_variant(plan)
+        assert v in (FUSED, PLAIN, PER_PASS) and (v == PLAIN) == (k == 0)
+        y = torch.empty_like(x)
+        sg.stencil_run(plan, x, y, 24)      # the tuned configuration as it stands
+        torch.cuda.synchronize()
+        assert torch.equal(y, plain)
+
+
+# ------------------------------------------------------------------- 3D
+SHAPES_3D = [(40, 70, 300), (23, 33, 129), (9, 100, 37)]
+
+
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_3d_int32_bit_exact(pattern, r, bkind):
+    sg = sgmod()
+    rng = np.random.default_rng(700 + 10 * r + pattern + 3 * bkind)
+    for shape in SHAPES_3D:
+        w = [float(x) for x in rng.integers(-2, 5, npoints(3, r, pattern))]
+        bval = 4321 if bkind == DIRICHLET else 0
+        n = shape[0] * shape[1] * shape[2]
+        u0 = uniform_u16(950 + shape[2], n).reshape(shape)
+        plan = sg.stencil_plan_create(3, r, shape, pattern, w, bkind, bval, sg.STENCIL_I32)
+        x = torch.from_numpy(u0).to(DEV)
+        kmax = sg.stencil_plan_max_k(plan)
+        for k in sorted({1, kmax}):
+            T = 2 * k + 1
+            ref = oracle.run_int(3, r, pattern, shape, w, bkind, bval, u0, T)
+            got = run(plan, x, T, k, FUSED).cpu().numpy()
+            np.testing.assert_array_equal(got, ref, err_msg=f"{shape} k={k} T={T}")
+            assert sg.stencil_plan_launch_count(plan, T) == 1 + (T % k > 0)
+
+
+@pytest.mark.parametrize("pattern", [STAR, BOX])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+def test_3d_fp32_identical_to_per_pass_plain_and_oracle(pattern, bkind):
+    sg = sgmod()
+    shape = SHAPES_3D[0]
+    w = list(np.random.default_rng(77 + pattern + bkind).uniform(-0.05, 0.2, npoints(3, 1, pattern)))
+    bval = 0.5 if bkind == DIRICHLET else 0.0
+    u0 = uniform01(1003, shape[0] * shape[1] * shape[2]).reshape(shape).astype(np.float32)
+    plan = sg.stencil_plan_create(3, 1, shape, pattern, w, bkind, bval, sg.STENCIL_F32)
+    x = torch.from_numpy(u0).to(DEV)
+    T = 17
+    ref = oracle.run(3, 1, pattern, shape, f32_weights(w), bkind, float(np.float32(bval)), u0.astype(np.float64), T)
+    plain = run(plan, x, T, 1, PLAIN)
+    assert normwise(plain.cpu().numpy(), ref) <= 1e-5
+    for k in range(1, sg.stencil_plan_max_k(plan) + 1):
+        assert torch.equal(run(plan, x, T, k, FUSED), plain), f"k={k}"
+        assert torch.equal(run(plan, x, T, k, PER_PASS), plain), f"k={k}"
+        for off in (1,):
+            assert torch.equal(run(plan, x, T, k, FUSED, offset=off), plain), f"k={k} offset={off}"
+    for planes in (1, 8, 13, 40):
+        sg.stencil_plan_set_tile_rows(plan, planes)
+        for k in (2, 4):
+            assert torch.equal(run(plan, x, T, k, FUSED), plain), f"planes={planes} k={k}"
+
+
+def test_3d_bench_size_sampled():
+    """512^3 FP32 3D7P, T = 32, at the tuned configuration: the persistent
+    launch bit-identical to the plain sweep (whose parity against the oracle
+    the dependency-cone tests establish)."""
+    sg = sgmod()
+    shape, T = (512, 512, 512), 32
+    w = [0.4] + [0.1] * 6
+    plan = sg.stencil_plan_create(3, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+    x = torch.rand(shape, device=DEV)
+    plain = run(plan, x, T, 1, PLAIN)
+    k, _ = sg.stencil_plan_tune(plan, T)
+    for kk in sorted({max(k, 1), 4}):
+        assert torch.equal(run(plan, x, T, kk, FUSED), plain), f"k={kk}"
