@@ -32,12 +32,21 @@ struct AdjParams {
     const float *lam_in;   // lam_{t+1}
     const float *u;        // u_t
     float *lam_out;        // lam_t
-    double *partials;      // [gridDim.x][np]
+    double *partials;      // [blocks][np]
     int64_t n0, n1, n2;
     int bkind;
     float bval;
     int first;             // 1: overwrite partials, 0: add
+    int vec_ok;            // rows and the three pointers allow float4 access
     float w[kMaxPts];      // evaluation (lexicographic) order
+};
+
+// Launch shape of one backward step: the rows kernel (grid-stride over
+// (plane, row block) pairs) where the extents allow it, else the generic one.
+struct AdjShape {
+    bool rows;
+    dim3 grid, block;
+    int nblocks;           // blocks = partial-sum slots
 };
 
 template <int D, int R, int PAT>
@@ -126,6 +135,147 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_step_kernel(const __grid_
     }
 }
 
+// The same backward step for grids with moderate extents (each extent
+// > 2r + RB + 2, 32-bit indices): a block of TX x TY threads covers TX groups
+// of 4 x-points and TY x RB rows; blocks walk the (plane, row block) pairs
+// with a grid stride, so the number of blocks -- and of FP64 partials -- stays
+// a few per SM.  Plane and row indices are uniform across a warp; halo rows
+// and columns wrap by one extent (periodic) or read 0 / the boundary value.
+template <int D, int R, int PAT, int RB>
+__global__ void __launch_bounds__(ADJ_THREADS) adjoint_rows_kernel(const __grid_constant__ AdjParams p) {
+    using Sh = Shape<D, R, PAT>;
+    constexpr int NP = Sh::npts, VX = ADJ_VX;
+    constexpr int NZ = D == 3 ? 2 * R + 1 : 1;
+    constexpr int NY = D >= 2 ? RB + 2 * R : 1;
+    constexpr int SP = VX + 2 * R;
+    __shared__ double red[ADJ_THREADS / 32][NP];
+    const int n0 = (int)p.n0, n1 = (int)p.n1, n2 = (int)p.n2;
+    const bool periodic = p.bkind == STENCIL_PERIODIC;
+    const float bval = p.bval;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int rows = (n1 + RB * (int)blockDim.y - 1) / (RB * (int)blockDim.y);   // row blocks per plane
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+    const bool full = x0 + VX <= n2;
+    const bool vec = full && p.vec_ok;
+    float gw[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) gw[j] = 0.f;
+    for (int rbk = blockIdx.y; rbk < n0 * rows; rbk += gridDim.y) {
+        const int i0 = rbk / rows;
+        const int i1b = ((rbk - i0 * rows) * (int)blockDim.y + (int)threadIdx.y) * RB;
+        if (x0 >= n2 || i1b >= n1) continue;
+        float lam[NZ][NY][SP], uu[NZ][NY][SP];
+#pragma unroll
+        for (int jz = 0; jz < NZ; ++jz) {
+            const int oz = D == 3 ? jz - R : 0;
+#pragma unroll
+            for (int jy = 0; jy < NY; ++jy) {
+                bool used = false, halo = false;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                    const int oy = D >= 2 ? jy - R - b : 0;
+                    if (D >= 2 && (oy < -R || oy > R)) continue;
+                    if (Sh::inc(oz, oy, 0)) used = true;
+                    if (PAT == STENCIL_BOX || (oz == 0 && oy == 0)) halo = true;
+                }
+                if (!used) continue;
+                int z = i0 + oz, y = D >= 2 ? i1b - R + jy : 0;
+                bool ok = true;
+                if (z < 0) { z += n0; ok = periodic; }
+                else if (z >= n0) { z -= n0; ok = periodic; }
+                if (y < 0) { y += n1; ok = ok && periodic; }
+                else if (y >= n1) { y -= n1; ok = ok && periodic; }
+                float *lr = lam[jz][jy], *ur = uu[jz][jy];
+                if (!ok) {
+#pragma unroll
+                    for (int q = 0; q < SP; ++q) { lr[q] = 0.f; ur[q] = bval; }
+                    continue;
+                }
+                const size_t base = ((size_t)z * n1 + y) * n2;
+                const float *lp = p.lam_in + base, *up = p.u + base;
+                if (vec) {
+                    const float4 a = __ldg(reinterpret_cast<const float4 *>(lp + x0));
+                    const float4 c = __ldg(reinterpret_cast<const float4 *>(up + x0));
+                    lr[R] = a.x; lr[R + 1] = a.y; lr[R + 2] = a.z; lr[R + 3] = a.w;
+                    ur[R] = c.x; ur[R + 1] = c.y; ur[R + 2] = c.z; ur[R + 3] = c.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VX; ++q) {   // last, partial group: wrap or outside value
+                        const int x = x0 + q;
+                        const bool in = x < n2;
+                        const int xx = in ? x : x - n2;
+                        lr[R + q] = (in || periodic) ? __ldg(lp + xx) : 0.f;
+                        ur[R + q] = (in || periodic) ? __ldg(up + xx) : bval;
+                    }
+                }
+                if (halo) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        int xl = x0 - R + q, xr = x0 + VX + q;
+                        const bool il = xl >= 0, ir = xr < n2;
+                        xl = il ? xl : xl + n2;
+                        xr = ir ? xr : xr - n2;
+                        lr[q] = (il || periodic) ? __ldg(lp + xl) : 0.f;
+                        ur[q] = (il || periodic) ? __ldg(up + xl) : bval;
+                        lr[R + VX + q] = (ir || periodic) ? __ldg(lp + xr) : 0.f;
+                        ur[R + VX + q] = (ir || periodic) ? __ldg(up + xr) : bval;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int yo = D >= 2 ? i1b + b : 0;
+            if (yo >= n1) break;
+            const int cz = D == 3 ? R : 0, cy = D >= 2 ? R + b : 0;   // this output's own row
+            float acc[VX];
+            bool first = true;
+#pragma unroll
+            for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz)
+#pragma unroll
+                for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy)
+#pragma unroll
+                    for (int ox = -R; ox <= R; ++ox) {
+                        if (!Sh::inc(oz, oy, ox)) continue;
+                        const int j = Sh::widx(oz, oy, ox);
+                        const float w = p.w[j];
+                        const float *lrow = lam[D == 3 ? R - oz : 0][D >= 2 ? R + b - oy : 0];   // row of x - o
+                        const float *urow = uu[D == 3 ? R + oz : 0][D >= 2 ? R + b + oy : 0];    // row of x + o
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const float l = lrow[R + v - ox];
+                            acc[v] = first ? __fmul_rn(w, l) : __fmaf_rn(w, l, acc[v]);
+                            if (full || x0 + v < n2) gw[j] = __fmaf_rn(lam[cz][cy][R + v], urow[R + v + ox], gw[j]);
+                        }
+                        first = false;
+                    }
+            float *out = p.lam_out + ((size_t)i0 * n1 + yo) * n2;
+            if (vec) {
+                *reinterpret_cast<float4 *>(out + x0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VX; ++v)
+                    if (x0 + v < n2) out[x0 + v] = acc[v];
+            }
+        }
+    }
+    // block sums of the weight-gradient terms in FP64, fixed order
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        double v = (double)gw[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = v;
+    }
+    __syncthreads();
+    if (tid < NP) {
+        double s = 0.0;
+        for (int wi = 0; wi < ADJ_THREADS / 32; ++wi) s += red[wi][tid];
+        double *dst = p.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NP + tid;
+        *dst = p.first ? s : *dst + s;
+    }
+}
+
 // grad_w[compact j] = sum over blocks of partials[b][eval j], fixed order
 __global__ void adjoint_wgrad_final(const double *__restrict__ partials, int nblocks, int np,
                                     const int *__restrict__ eval_to_compact, double *grad_w) {
@@ -144,17 +294,50 @@ __global__ void adjoint_wgrad_final(const double *__restrict__ partials, int nbl
     }
 }
 
+// rows per thread in the rows kernel: two where the loaded rows stay few
+constexpr int adj_rb(int d, int pat) { return (d >= 2 && !(d == 3 && pat == STENCIL_BOX)) ? 2 : 1; }
+
+static AdjShape adj_shape(const stencil_plan_s &P) {
+    AdjShape a;
+    const int64_t n0 = P.n[0], n1 = P.n[1], n2 = P.n[2], r = P.r;
+    const int rb = adj_rb(P.dim, P.pattern);
+    const int64_t groups = (n2 + ADJ_VX - 1) / ADJ_VX;
+    const int tx = (int)std::min<int64_t>(ADJ_THREADS, (groups + 31) / 32 * 32);
+    const int ty = ADJ_THREADS / tx;
+    const int64_t bx = (groups + tx - 1) / tx;
+    const int64_t rowblocks = n0 * ((n1 + (int64_t)rb * ty - 1) / ((int64_t)rb * ty));
+    a.rows = (P.dim < 3 || n0 > 2 * r + 2) && (P.dim < 2 || n1 > 2 * r + rb + 2) && n2 >= 2 * (ADJ_VX + r) &&
+             n0 < (1ll << 30) && n1 < (1ll << 30) && n2 < (1ll << 30) && rowblocks < (1ll << 31) && bx <= 65535;
+    if (a.rows) {
+        // about 16 blocks per SM in all, each walking several row blocks
+        const int64_t want = std::max<int64_t>(1, (int64_t)P.sm_count * 16 / bx);
+        const int64_t by = std::min<int64_t>(std::min<int64_t>(rowblocks, want), 65535);
+        a.grid = dim3((unsigned)bx, (unsigned)by, 1);
+        a.block = dim3((unsigned)tx, (unsigned)ty, 1);
+        a.nblocks = (int)(bx * by);
+    } else {
+        const int64_t items = n0 * n1 * groups;
+        int64_t nb = (items + ADJ_THREADS - 1) / ADJ_THREADS;
+        nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)P.sm_count * 8));
+        a.grid = dim3((unsigned)nb, 1, 1);
+        a.block = dim3(ADJ_THREADS, 1, 1);
+        a.nblocks = (int)nb;
+    }
+    return a;
+}
+
 template <int D, int R, int PAT>
-static cudaError_t launch_adj_t(const AdjParams &p, int nblocks, cudaStream_t st) {
-    adjoint_step_kernel<D, R, PAT><<<nblocks, ADJ_THREADS, 0, st>>>(p);
+static cudaError_t launch_adj_t(const AdjParams &p, const AdjShape &a, cudaStream_t st) {
+    if (a.rows) adjoint_rows_kernel<D, R, PAT, adj_rb(D, PAT)><<<a.grid, a.block, 0, st>>>(p);
+    else adjoint_step_kernel<D, R, PAT><<<a.grid, a.block, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-static cudaError_t launch_adj(const stencil_plan_s &P, const AdjParams &p, int nblocks, cudaStream_t st) {
+static cudaError_t launch_adj(const stencil_plan_s &P, const AdjParams &p, const AdjShape &a, cudaStream_t st) {
     const bool box = P.pattern == STENCIL_BOX;
 #define SG_ADJ(DD, RR)                                                                                  \
-    if (P.dim == DD && P.r == RR) return box ? launch_adj_t<DD, RR, STENCIL_BOX>(p, nblocks, st)        \
-                                             : launch_adj_t<DD, RR, STENCIL_STAR>(p, nblocks, st);
+    if (P.dim == DD && P.r == RR) return box ? launch_adj_t<DD, RR, STENCIL_BOX>(p, a, st)              \
+                                             : launch_adj_t<DD, RR, STENCIL_STAR>(p, a, st);
     SG_ADJ(1, 1) SG_ADJ(1, 2) SG_ADJ(2, 1) SG_ADJ(2, 2) SG_ADJ(3, 1) SG_ADJ(3, 2)
 #undef SG_ADJ
     return cudaErrorInvalidValue;
@@ -190,11 +373,8 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
     const int64_t M = (T + c - 1) / c;   // segments
     // workspace: checkpoints 1..M-1, c-1 recomputed states, two lam grids
     const size_t ngrids = (size_t)(M - 1) + (size_t)(c - 1) + 2;
-    const int64_t groups = (P->n[2] + ADJ_VX - 1) / ADJ_VX;
-    const int64_t items = P->n[0] * P->n[1] * groups;
-    int64_t nb = (items + ADJ_THREADS - 1) / ADJ_THREADS;
-    nb = std::min<int64_t>(nb, (int64_t)P->sm_count * 8);
-    const int nblocks = (int)std::max<int64_t>(1, nb);
+    const AdjShape shape = adj_shape(*P);
+    const int nblocks = shape.nblocks;
     const size_t need = ngrids * gb + 256 + sizeof(double) * (size_t)nblocks * P->np + sizeof(int) * P->np;
     if (P->adj_ws_bytes < need) {
         cudaFree(P->adj_ws);
@@ -247,7 +427,9 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
             p.lam_in = lam_next;
             p.lam_out = static_cast<float *>(t == 0 ? grad_u0 : lam[li]);
             p.first = first ? 1 : 0;
-            e = launch_adj(*P, p, nblocks, st);
+            p.vec_ok = (P->n[2] % 4 == 0) && ((uintptr_t)p.u % 16 == 0) && ((uintptr_t)p.lam_in % 16 == 0) &&
+                       ((uintptr_t)p.lam_out % 16 == 0);
+            e = launch_adj(*P, p, shape, st);
             if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
             first = false;
             lam_next = p.lam_out;

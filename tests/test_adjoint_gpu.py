@@ -30,6 +30,10 @@ CASES = [
     (2, 2, STAR, (33, 30), PERIODIC, 0.0, 10, 10),
     (1, 1, STAR, (301,), DIRICHLET, 0.5, 25, 6),
     (1, 2, STAR, (77,), PERIODIC, 0.0, 8, 1),
+    # extents too small for the row-block kernel: the generic step kernel
+    (3, 1, STAR, (3, 4, 5), PERIODIC, 0.0, 5, 2),
+    (2, 2, BOX, (5, 6), DIRICHLET, 0.1, 4, 2),
+    (1, 1, STAR, (7,), PERIODIC, 0.0, 6, 3),
 ]
 
 
