@@ -167,11 +167,20 @@ __device__ __forceinline__ void load_row_reg(const typename Traits<DT>::S *__res
             for (int v = 0; v < V; ++v) out[v] = bval;
             return;
         }
-        y = wrap_idx(y, ny);
+        y = y < 0 ? y + ny : y - ny;
+        if (y < 0 || y >= ny) y = wrap_idx(y, ny);
     }
     const typename Traits<DT>::S *row = src + y * nx;
-    if (vec_ok && xl >= 0 && xl + V <= nx) {
-        ldvec<DT, COH>(row + xl, out);
+    // a lane's V elements outside a periodic row, wrapped by one extent, are
+    // still one vector when the row length is a multiple of V
+    int64_t xs = xl;
+    bool xin = xl >= 0 && xl + V <= nx;
+    if (!xin && periodic) {
+        xs = xl < 0 ? xl + nx : xl - nx;
+        xin = xs >= 0 && xs + V <= nx;
+    }
+    if (vec_ok && xin) {
+        ldvec<DT, COH>(row + xs, out);
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) {

@@ -112,7 +112,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 // Copy window plane z (virtual, wrapped or boundary) into a stage, every
 // thread a share, with cp.async (4-byte elements) or plain stores of the
-// boundary value.  Used for periodic grids and rows TMA cannot address.
+// boundary value.  Used for periodic grids and rows TMA cannot address.  A
+// thread copies the same 16-byte column chunk of several rows; a chunk that
+// lies outside a periodic grid is wrapped by one extent, and when the grid's
+// rows are 16-byte multiples it is still one aligned 16-byte copy.
 template <int DT>
 __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, const typename Traits<DT>::S *src,
                                                  int64_t nx, int64_t ny, int64_t nz, bool periodic,
@@ -122,23 +125,37 @@ __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, 
     using G = F3Geo<DT, 1, 1>;
     constexpr int W = G::W;
     constexpr int VE = 16 / (int)sizeof(S);   // elements per 16-byte copy
+    constexpr int TPR = W / VE;               // threads per window row
+    constexpr int RSTEP = F3_THREADS / TPR;   // rows per sweep of the block
+    static_assert(W % VE == 0 && F3_THREADS % TPR == 0, "chunking");
     bool zin = z >= 0 && z < nz;
     if (!zin && periodic) { z = wrap_idx(z, nz); zin = true; }
-    for (int e = threadIdx.x * VE; e < W * F3_WY; e += F3_THREADS * VE) {
-        const int row = e / W, col = e - row * W;
+    const int col = (int)(threadIdx.x % TPR) * VE;
+    const int64_t x0 = xw0 + col;
+    int64_t xs = x0;
+    bool xin = x0 >= 0 && x0 + VE <= nx;
+    if (!xin && periodic) {
+        xs = x0 < 0 ? x0 + nx : x0 - nx;
+        xin = xs >= 0 && xs + VE <= nx;
+    }
+    const bool fast = vec_ok && xin;
+    for (int row = (int)(threadIdx.x / TPR); row < F3_WY; row += RSTEP) {
         int64_t y = yw0 + row;
         bool yin = y >= 0 && y < ny;
-        if (!yin && periodic) { y = wrap_idx(y, ny); yin = true; }
-        const int64_t x0 = xw0 + col;
-        S *d = stage + e;
+        if (!yin && periodic) {
+            y = y < 0 ? y + ny : y - ny;
+            if (y < 0 || y >= ny) y = wrap_idx(y, ny);
+            yin = true;
+        }
+        S *d = stage + row * W + col;
         if (!(zin && yin)) {
 #pragma unroll
             for (int q = 0; q < VE; ++q) d[q] = from_c<S>(bval);
             continue;
         }
         const S *rowp = src + (z * ny + y) * nx;
-        if (vec_ok && x0 >= 0 && x0 + VE <= nx) {
-            cp_async16(d, rowp + x0);
+        if (fast) {
+            cp_async16(d, rowp + xs);
         } else {
 #pragma unroll
             for (int q = 0; q < VE; ++q) {
