@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_step_kernel(const __grid_
         for (int v = 0; v < ADJ_VX; ++v)
             if (x0 + v < n2) out[x0 + v] = acc[v];
     }
-    // block sums of the weight-gradient terms in FP64, fixed order
+    // block sums of the weight-gradient terms (warp tree in FP32, warps in FP64)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        double v = (double)gw[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][j] = v;
+        float v = gw[j];
+        for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (lane == 0) red[warp][j] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < NP) {
@@ -141,8 +141,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_step_kernel(const __grid_
 // with a grid stride, so the number of blocks -- and of FP64 partials -- stays
 // a few per SM.  Plane and row indices are uniform across a warp; halo rows
 // and columns wrap by one extent (periodic) or read 0 / the boundary value.
+// resident blocks per SM the register allocation must allow (r = 2 and the
+// 3D box keep larger neighbourhoods in registers)
+constexpr int adj_min_blocks(int d, int r, int pat) { return r == 1 && !(d == 3 && pat == STENCIL_BOX) ? 3 : 1; }
+
 template <int D, int R, int PAT, int RB>
-__global__ void __launch_bounds__(ADJ_THREADS) adjoint_rows_kernel(const __grid_constant__ AdjParams p) {
+__global__ void __launch_bounds__(ADJ_THREADS, adj_min_blocks(D, R, PAT)) adjoint_rows_kernel(const __grid_constant__ AdjParams p) {
     using Sh = Shape<D, R, PAT>;
     constexpr int NP = Sh::npts, VX = ADJ_VX;
     constexpr int NZ = D == 3 ? 2 * R + 1 : 1;
@@ -259,13 +263,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_rows_kernel(const __grid_
             }
         }
     }
-    // block sums of the weight-gradient terms in FP64, fixed order
+    // block sums of the weight-gradient terms, fixed order: the warp tree in
+    // FP32 (each lane's term is already an FP32 sum; a 32-lane FP64 tree
+    // would occupy the FP64 pipe -- 2 operations per clock per SM -- for a
+    // third of the kernel), the warps' sums and the running partials in FP64
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        double v = (double)gw[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][j] = v;
+        float v = gw[j];
+        for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (lane == 0) red[warp][j] = (double)v;
     }
     __syncthreads();
     if (tid < NP) {
@@ -295,7 +302,7 @@ __global__ void adjoint_wgrad_final(const double *__restrict__ partials, int nbl
 }
 
 // rows per thread in the rows kernel: two where the loaded rows stay few
-constexpr int adj_rb(int d, int pat) { return (d >= 2 && !(d == 3 && pat == STENCIL_BOX)) ? 2 : 1; }
+constexpr int adj_rb(int d, int pat) { return d == 2 ? 2 : 1; }
 
 static AdjShape adj_shape(const stencil_plan_s &P) {
     AdjShape a;
