@@ -2,7 +2,10 @@
 //
 // Not in the paper (which runs one grid at a time): grids of uneven size and
 // step count share the GPU through a work queue.  Each grid's passes (k
-// fused steps, the last one T mod k) are cut into warp-sized tiles (one
+// fused steps; the first one the remainder T - (passes - 1) k, so that only
+// pass 0 mixes fusion depths -- and instruction streams -- across grids,
+// the result being the same for any grouping of the steps) are cut into
+// warp-sized tiles (one
 // column band x Ly rows).  Items (grid, pass, tile) are listed pass-major;
 // worker warps take the next item from an atomic ticket, wait until every
 // tile whose output meets the item's input window (wrapped for periodic
@@ -40,7 +43,7 @@ template <typename C> struct BatchGrid {
     void *out;
     void *ws;
     int ny, nx;
-    int passes, k_last;
+    int passes, k_first;   // the first pass advances k_first <= KB steps, the others KB
     int bands, chunks;
     int tile_base;       // index of this grid's first tile counter
     int boff, coff;      // this grid's band / chunk offsets into dep_off
@@ -72,7 +75,7 @@ __device__ __forceinline__ void batch_job(const BatchGrid<typename Traits<DT>::C
                                           const typename Traits<DT>::C *wr, int64_t xo0, int64_t yo0, int64_t yo1,
                                           bool vec_ok, uint32_t &gst, int lane) {
     using S = typename Traits<DT>::S;
-    // tiles are cut with k = KB's band width; a shorter last pass must write
+    // tiles are cut with k = KB's band width; a shorter first pass must write
     // exactly the same columns
     static_assert(F2Geo<DT, R, K>::BW == F2Geo<DT, R, KB>::BW, "band width must not depend on k <= KB");
     fused2d_job<DT, R, PAT, K, PROD_REG, true, MASK>(nullptr, static_cast<const S *>(src), static_cast<S *>(dst),
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant
         // buffers: the last pass writes `out`, earlier ones alternate ws / out
         const void *src = pass == 0 ? G.in : (((G.passes - pass) % 2 == 0) ? G.out : G.ws);
         void *dst = ((G.passes - 1 - pass) % 2 == 0) ? G.out : G.ws;
-        const int kp = pass == G.passes - 1 ? G.k_last : KB;
+        const int kp = pass == 0 ? G.k_first : KB;
         C wr[Sh::npts];
 #pragma unroll
         for (int j = 0; j < Sh::npts; ++j) wr[j] = G.w[j];
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant
         const int64_t yo0 = (int64_t)c * BT_LY;
         const int64_t yo1 = yo0 + BT_LY < G.ny ? yo0 + BT_LY : G.ny;
         const bool vec_ok = (G.nx % Traits<DT>::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
-        // tiles are laid out with the band width of k = KB; shorter last
+        // tiles are laid out with the band width of k = KB; shorter first
         // passes use the same tiles (their halo is smaller)
         const bool interior = !dir || (xo0 - Geo::H >= 0 && xo0 - Geo::H + Geo::W <= G.nx && yo0 - R * KB >= 0 &&
                                        yo1 + R * KB <= G.ny);
@@ -219,7 +222,7 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
         G.nx = (int)B->nx[g];
         const int64_t T = B->T[g];
         G.passes = (int)((T + B->kb - 1) / B->kb);
-        G.k_last = (int)(T - (int64_t)(G.passes - 1) * B->kb);
+        G.k_first = (int)(T - (int64_t)(G.passes - 1) * B->kb);
         G.bands = (G.nx + bw - 1) / bw;
         G.chunks = (G.ny + BT_LY - 1) / BT_LY;
         G.tile_base = (int)tiles;

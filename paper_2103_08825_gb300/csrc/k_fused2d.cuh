@@ -154,6 +154,32 @@ __device__ __forceinline__ void ldsvec(const typename Traits<DT>::S *p, typename
     }
 }
 
+// V values returned by value (registers) from an out-of-line function
+template <typename C, int V> struct LaneVals {
+    C v[V];
+};
+
+// The rare cases of load_row_reg, kept out of line so that the unrolled job
+// loops hold only the vector path: a row wrapped more than once, and lanes
+// whose V elements straddle the row's end or cannot be read as one vector.
+template <int DT, bool COH>
+__device__ __noinline__ LaneVals<typename Traits<DT>::C, Traits<DT>::V> load_row_edge(
+    const typename Traits<DT>::S *__restrict__ src, int64_t nx, int64_t ny, bool periodic,
+    typename Traits<DT>::C bval, int64_t y, int64_t xl) {
+    constexpr int V = Traits<DT>::V;
+    LaneVals<typename Traits<DT>::C, V> r;
+    y = wrap_idx(y, ny);
+    const typename Traits<DT>::S *row = src + y * nx;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int64_t x = xl + v;
+        if (x >= 0 && x < nx) r.v[v] = to_c(ldx<COH>(row + x));
+        else if (periodic) r.v[v] = to_c(ldx<COH>(row + wrap_idx(x, nx)));
+        else r.v[v] = bval;
+    }
+    return r;
+}
+
 // One lane's V elements of virtual row y, columns xl..xl+V-1, through the
 // boundary rule (PROD_REG input path).
 template <int DT, bool COH>
@@ -168,9 +194,7 @@ __device__ __forceinline__ void load_row_reg(const typename Traits<DT>::S *__res
             return;
         }
         y = y < 0 ? y + ny : y - ny;
-        if (y < 0 || y >= ny) y = wrap_idx(y, ny);
     }
-    const typename Traits<DT>::S *row = src + y * nx;
     // a lane's V elements outside a periodic row, wrapped by one extent, are
     // still one vector when the row length is a multiple of V
     int64_t xs = xl;
@@ -179,16 +203,12 @@ __device__ __forceinline__ void load_row_reg(const typename Traits<DT>::S *__res
         xs = xl < 0 ? xl + nx : xl - nx;
         xin = xs >= 0 && xs + V <= nx;
     }
-    if (vec_ok && xin) {
-        ldvec<DT, COH>(row + xs, out);
+    if (vec_ok && xin && y >= 0 && y < ny) {
+        ldvec<DT, COH>(src + y * nx + xs, out);
     } else {
+        const LaneVals<typename Traits<DT>::C, V> r = load_row_edge<DT, COH>(src, nx, ny, periodic, bval, y, xl);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            int64_t x = xl + v;
-            if (x >= 0 && x < nx) out[v] = to_c(ldx<COH>(row + x));
-            else if (periodic) out[v] = to_c(ldx<COH>(row + wrap_idx(x, nx)));
-            else out[v] = bval;
-        }
+        for (int v = 0; v < V; ++v) out[v] = r.v[v];
     }
 }
 
