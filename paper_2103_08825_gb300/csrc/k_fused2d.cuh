@@ -772,24 +772,33 @@ cudaError_t launch_f2mp_k(const stencil_plan_s &P, const void *src0, void *de, v
     return cudaErrorInvalidValue;
 }
 
+// One radius, both patterns, every k: each (dtype, radius) is instantiated in
+// a translation unit of its own, so that the build compiles them in parallel.
+template <int DT, int R>
+cudaError_t launch_f2_r(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    return P.pattern == STENCIL_BOX ? launch_f2_k<DT, R, STENCIL_BOX>(P, src, dst, k, st)
+                                    : launch_f2_k<DT, R, STENCIL_STAR>(P, src, dst, k, st);
+}
+
+template <int DT, int R>
+cudaError_t launch_f2mp_r(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                          cudaStream_t st) {
+    return P.pattern == STENCIL_BOX ? launch_f2mp_k<DT, R, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                                    : launch_f2mp_k<DT, R, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+}
+
 template <int DT>
 cudaError_t launch_f2mp_dt(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
                            cudaStream_t st) {
-    const bool box = P.pattern == STENCIL_BOX;
-    if (P.r == 1) return box ? launch_f2mp_k<DT, 1, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
-                             : launch_f2mp_k<DT, 1, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
-    if (P.r == 2) return box ? launch_f2mp_k<DT, 2, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
-                             : launch_f2mp_k<DT, 2, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+    if (P.r == 1) return launch_f2mp_r<DT, 1>(P, src0, de, dof, k, passes, st);
+    if (P.r == 2) return launch_f2mp_r<DT, 2>(P, src0, de, dof, k, passes, st);
     return cudaErrorInvalidValue;
 }
 
 template <int DT>
 cudaError_t launch_f2_dt(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
-    const bool box = P.pattern == STENCIL_BOX;
-    if (P.r == 1) return box ? launch_f2_k<DT, 1, STENCIL_BOX>(P, src, dst, k, st)
-                             : launch_f2_k<DT, 1, STENCIL_STAR>(P, src, dst, k, st);
-    if (P.r == 2) return box ? launch_f2_k<DT, 2, STENCIL_BOX>(P, src, dst, k, st)
-                             : launch_f2_k<DT, 2, STENCIL_STAR>(P, src, dst, k, st);
+    if (P.r == 1) return launch_f2_r<DT, 1>(P, src, dst, k, st);
+    if (P.r == 2) return launch_f2_r<DT, 2>(P, src, dst, k, st);
     return cudaErrorInvalidValue;
 }
 

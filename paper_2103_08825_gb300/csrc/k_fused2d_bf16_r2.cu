@@ -1,0 +1,7 @@
+// k_fused2d_bf16_r2.cu -- instantiations of the 2D fused kernel for
+// STENCIL_BF16 storage, radius 2 (own translation unit: the build compiles in parallel).
+#include "k_fused2d.cuh"
+
+namespace sg {
+template cudaError_t launch_f2_r<STENCIL_BF16, 2>(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+}  // namespace sg

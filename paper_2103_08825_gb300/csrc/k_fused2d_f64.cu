@@ -1,8 +1,11 @@
 // k_fused2d_f64.cu -- instantiations of the 2D fused kernel for STENCIL_F64
-// storage (one translation unit per dtype keeps the build parallel).
+// storage, radius 1, and the dispatcher (radius 2 is instantiated in
+// k_fused2d_f64_r2.cu: one translation unit each keeps the build parallel).
 #include "k_fused2d.cuh"
 
 namespace sg {
+extern template cudaError_t launch_f2_r<STENCIL_F64, 2>(const stencil_plan_s &, const void *, void *, int,
+                                                          cudaStream_t);
 cudaError_t launch_f2_F64(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
     return launch_f2_dt<STENCIL_F64>(P, src, dst, k, st);
 }
