@@ -287,6 +287,7 @@ stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
     cudaFree(P->adj_ws);
     cudaFree(P->adj_partials);
     cudaFree(P->d_mp);
+    cudaFree(P->d_skip);
     cudaSetDevice(cur);
     delete P;
     return STENCIL_OK;
@@ -515,6 +516,20 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     P->tuned_plain = best_plain;
     if (best_k) *best_k = best_plain ? 0 : bk;
     if (best_ms) *best_ms = bms;
+    return STENCIL_OK;
+}
+
+// Test hook (not in the public header): item q of the plan's persistent
+// multi-pass launches skips its completion publish, so that the items that
+// depend on it must give up their bounded waits -- host-side fault injection
+// for the timeout path.  q < 0 disables.
+stencil_status_t stencil_plan_test_skip_publish(stencil_plan_t P, int64_t q) {
+    if (!P) return STENCIL_ERR_INVALID_ARG;
+    if (!P->d_skip) {
+        if (cudaMalloc(&P->d_skip, sizeof(int)) != cudaSuccess) return STENCIL_ERR_OOM;
+    }
+    const int v = q < 0 ? -1 : (int)q;
+    if (cudaMemcpy(P->d_skip, &v, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return STENCIL_ERR_CUDA;
     return STENCIL_OK;
 }
 

@@ -95,6 +95,7 @@ template <typename C> struct F2MpParams {
                        // the whole other half is cleared, whatever its next tiling)
     int tiles, cap;
     int parity;
+    const int *skip;   // test hook: the item whose completion is never published (null: none)
     C w[25];
 };
 
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
         }
         // publish: every lane's stores, then (release) the tile's pass count
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && !(p.skip && *p.skip == (long long)t)) {
             if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
         }
@@ -727,6 +728,7 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
     p.cap = (int)P.mp_tiles_cap;
     p.parity = (int)(P.mp_seq++ & 1u);
+    p.skip = P.d_skip;
     const int64_t jobs = (int64_t)p.tiles * passes;
     int64_t grid = (jobs + F2_NW - 1) / F2_NW;
     if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;

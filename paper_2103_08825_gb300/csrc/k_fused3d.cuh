@@ -83,6 +83,7 @@ template <typename C> struct F3MpParams {
     int *done;              // [2][cap]: passes each tile has finished
     int tiles, cap;
     int parity;
+    const int *skip;        // test hook: the item whose completion is never published (null: none)
     C w[125];
 };
 
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             return;
         }
         // fused3d_job ends with a barrier after the CTA's last stores: publish
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !(p.skip && *p.skip == (long long)t)) {
             if constexpr (PROD == PROD3_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
         }
@@ -777,6 +778,7 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
     p.cap = (int)P.mp_tiles_cap;
     p.parity = (int)(P.mp_seq++ & 1u);
+    p.skip = P.d_skip;
     const int64_t jobs = tiles * passes;
     const int64_t grid = jobs < slots ? jobs : slots;
     kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(maps[0], maps[1], maps[2], p);

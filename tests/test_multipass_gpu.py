@@ -243,3 +243,30 @@ def test_3d_bench_size_sampled():
     k, _ = sg.stencil_plan_tune(plan, T)
     for kk in sorted({max(k, 1), 4}):
         assert torch.equal(run(plan, x, T, kk, FUSED), plain), f"k={kk}"
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dependency_timeout_is_reported_and_recovers(dim):
+    """Host-side fault injection: one tile of pass 0 never publishes its
+    completion, so the tiles of pass 1 that read it must give up their bounded
+    waits (about one second), raise the abort flag and report
+    STENCIL_ERR_TIMEOUT; the context stays usable and the next run (the
+    other counter parity, cleared by the aborted launch) is correct."""
+    import time
+    sg = sgmod()
+    shape = (300, 500) if dim == 2 else (40, 70, 300)
+    w = [0.5, 0.125, 0.125, 0.125, 0.125] if dim == 2 else [0.4] + [0.1] * 6
+    plan = sg.stencil_plan_create(dim, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+    x = torch.rand(shape, device=DEV)
+    plain = run(plan, x, 8, 1, PLAIN)
+    sg.stencil_plan_set_variant(plan, FUSED)
+    sg.stencil_plan_set_k(plan, 2)
+    assert sg.load().stencil_plan_test_skip_publish(plan.handle, 0) == 0
+    y = torch.empty_like(x)
+    t0 = time.time()
+    sg.stencil_run(plan, x, y, 8)
+    assert sg.stencil_get_device_status(plan) == sg.STENCIL_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    assert sg.load().stencil_plan_test_skip_publish(plan.handle, -1) == 0
+    for _ in range(2):
+        assert torch.equal(run(plan, x, 8, 2, FUSED), plain)
