@@ -70,9 +70,8 @@ typedef enum { STENCIL_STAR = 0, STENCIL_BOX = 1 } stencil_pattern_t;
 typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_kind_t;
 
 /* Which kernels stencil_run uses.  FUSED: k steps per pass (the default);
- * for 2D and 3D grids the passes of exactly k steps run as one persistent
- * launch whose tiles wait on their neighbours' completion of the previous
- * pass.
+ * the passes of exactly k steps run as one persistent launch whose tiles
+ * wait on their neighbours' completion of the previous pass.
  * PLAIN: one step per launch, each thread reading its own neighbours -- the
  * one-step-per-launch sweep the fused path is measured against.
  * FUSED_PER_PASS: the fused kernels with one launch per pass. */
@@ -123,16 +122,17 @@ stencil_status_t stencil_plan_get_variant(stencil_plan_t plan, int32_t *variant)
 
 /* Tile length of the fused kernels along the outermost dimension: in 2D the
  * rows one warp job advances (at least max(4 r k, 16)), in 3D the z planes
- * one CTA job advances (at least max(4 r k, 8)); at most the grid's extent
- * is used.  0 selects the default (about two to three jobs per resident warp
- * or CTA per pass).  1D plans keep the value and ignore it. */
+ * one CTA job advances (at least max(4 r k, 8)), in 1D the vector sets of
+ * 32 x (2 FP64, else 4) elements one warp job of the persistent launch
+ * advances; at most the grid's extent is used.  0 selects
+ * the default (about two to three jobs per resident warp or CTA per pass). */
 stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t plan, int32_t rows);
 stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t plan, int32_t *rows);
 
-/* Autotune the fusion depth, the launch form and (2D, 3D) the tile length:
+/* Autotune the fusion depth, the launch form and the tile length:
  * times stencil_run for the one-step kernel and, for every supported k, the
- * fused kernels with one launch per pass and -- in 2D and 3D -- the
- * persistent multi-pass launch with each of a few tile lengths, on
+ * fused kernels with one launch per pass and the persistent multi-pass
+ * launch with each of a few tile lengths, on
  * plan-owned buffers holding zeros, with CUDA events on `stream`, and keeps
  * the fastest (for tiny or FP64-pipe-bound grids the one-step kernel can
  * win).  Synchronises `stream`.  `T` is the step count to tune for; best_k
@@ -144,7 +144,7 @@ stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t plan, int32_t *rows);
 stencil_status_t stencil_plan_tune(stencil_plan_t plan, int64_t T, void *stream, int32_t *best_k, double *best_ms);
 
 /* Number of kernel launches stencil_run makes for T steps with the current
- * variant and k: T plain steps, ceil(T/k) fused passes, or for the 2D/3D
+ * variant and k: T plain steps, ceil(T/k) fused passes, or for the
  * persistent form one launch plus one for a last pass of T mod k steps. */
 stencil_status_t stencil_plan_launch_count(stencil_plan_t plan, int64_t T, int64_t *launches);
 

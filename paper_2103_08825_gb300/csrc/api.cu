@@ -459,6 +459,9 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     if (P->dim == 3)
         for (int r : {16, 32, 48, 64})
             if (r < P->n[0]) rows_c.push_back(r);
+    if (P->dim == 1)
+        for (int r : {2, 4, 8, 16, 32})
+            if (r * 128 < P->n[2]) rows_c.push_back(r);
     // candidates: the one-step kernel (k = 0 here), then every fused depth,
     // one launch per pass (default tiles) and -- where the grid allows it --
     // the persistent multi-pass launch with each tile length

@@ -136,11 +136,12 @@ cudaError_t launch_fused3d_multi(const stencil_plan_s &P, const void *src0, void
 }
 
 bool fused_multi_ok(const stencil_plan_s &P, int k) {
-    return P.dim == 2 ? fused2d_multi_ok(P, k) : P.dim == 3 ? fused3d_multi_ok(P, k) : false;
+    return P.dim == 1 ? fused1d_multi_ok(P, k) : P.dim == 2 ? fused2d_multi_ok(P, k) : fused3d_multi_ok(P, k);
 }
 
 cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
                                int passes, cudaStream_t st) {
+    if (P.dim == 1) return launch_fused1d_multi(P, src0, dst_even, dst_odd, k, passes, st);
     if (P.dim == 2) return launch_fused2d_multi(P, src0, dst_even, dst_odd, k, passes, st);
     if (P.dim == 3) return launch_fused3d_multi(P, src0, dst_even, dst_odd, k, passes, st);
     return cudaErrorNotSupported;

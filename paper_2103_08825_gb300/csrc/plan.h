@@ -72,9 +72,12 @@ cudaError_t launch_fused2d_multi(const stencil_plan_s &P, const void *src0, void
                                  int passes, cudaStream_t st);
 bool fused2d_multi_ok(const stencil_plan_s &P, int k);
 bool fused3d_multi_ok(const stencil_plan_s &P, int k);
+bool fused1d_multi_ok(const stencil_plan_s &P, int k);
+cudaError_t launch_fused1d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
+                                 int passes, cudaStream_t st);
 cudaError_t launch_fused3d_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
                                  int passes, cudaStream_t st);
-// the persistent multi-pass form for the plan's dimension (2D or 3D)
+// the persistent multi-pass form for the plan's dimension
 bool fused_multi_ok(const stencil_plan_s &P, int k);
 cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *dst_even, void *dst_odd, int k,
                                int passes, cudaStream_t st);

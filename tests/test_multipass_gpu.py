@@ -245,7 +245,7 @@ def test_3d_bench_size_sampled():
         assert torch.equal(run(plan, x, T, kk, FUSED), plain), f"k={kk}"
 
 
-@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 def test_dependency_timeout_is_reported_and_recovers(dim):
     """Host-side fault injection: one tile of pass 0 never publishes its
     completion, so the tiles of pass 1 that read it must give up their bounded
@@ -254,8 +254,8 @@ def test_dependency_timeout_is_reported_and_recovers(dim):
     other counter parity, cleared by the aborted launch) is correct."""
     import time
     sg = sgmod()
-    shape = (300, 500) if dim == 2 else (40, 70, 300)
-    w = [0.5, 0.125, 0.125, 0.125, 0.125] if dim == 2 else [0.4] + [0.1] * 6
+    shape = {1: (100003,), 2: (300, 500), 3: (40, 70, 300)}[dim]
+    w = {1: [0.25, 0.5, 0.25], 2: [0.5, 0.125, 0.125, 0.125, 0.125], 3: [0.4] + [0.1] * 6}[dim]
     plan = sg.stencil_plan_create(dim, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
     x = torch.rand(shape, device=DEV)
     plain = run(plan, x, 8, 1, PLAIN)
@@ -270,3 +270,35 @@ def test_dependency_timeout_is_reported_and_recovers(dim):
     assert sg.load().stencil_plan_test_skip_publish(plan.handle, -1) == 0
     for _ in range(2):
         assert torch.equal(run(plan, x, 8, 2, FUSED), plain)
+
+
+
+# ------------------------------------------------------------------- 1D
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("bkind", [DIRICHLET, PERIODIC])
+@pytest.mark.parametrize("n", [5, 300, 257, 4097, 65536, 100003])
+def test_1d_int32_bit_exact_and_fp64_identical(r, bkind, n):
+    sg = sgmod()
+    rng = np.random.default_rng(800 + r + 3 * bkind + n % 97)
+    w = [float(x) for x in rng.integers(-3, 8, 2 * r + 1)]
+    bval = 99 if bkind == DIRICHLET else 0
+    u0 = uniform_u16(960 + n, n)
+    plan = sg.stencil_plan_create(1, r, (n,), STAR, w, bkind, bval, sg.STENCIL_I32)
+    x = torch.from_numpy(u0).to(DEV)
+    for k in (1, 3, 8):
+        for T in (2 * k, 3 * k + 2):
+            ref = oracle.run_int(1, r, STAR, (n,), w, bkind, bval, u0, T)
+            np.testing.assert_array_equal(run(plan, x, T, k, FUSED).cpu().numpy(), ref, err_msg=f"k={k} T={T}")
+    wf = list(rng.uniform(0.05, 0.3, 2 * r + 1))
+    u = uniform01(961 + n, n)
+    pf = sg.stencil_plan_create(1, r, (n,), STAR, wf, bkind, 0.25 if bkind == DIRICHLET else 0.0, sg.STENCIL_F64)
+    xf = torch.from_numpy(u).to(DEV)
+    T = 37
+    ref = oracle.run(1, r, STAR, (n,), wf, bkind, 0.25 if bkind == DIRICHLET else 0.0, u, T)
+    plain = run(pf, xf, T, 1, PLAIN)
+    assert normwise(plain.cpu().numpy(), ref) <= 1e-12
+    for k in (1, 2, 5, 8):
+        assert torch.equal(run(pf, xf, T, k, FUSED), plain), f"k={k}"
+    for cpj in (1, 13, 40):
+        sg.stencil_plan_set_tile_rows(pf, cpj)
+        assert torch.equal(run(pf, xf, T, 4, FUSED), plain), f"cpj={cpj}"
