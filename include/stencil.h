@@ -156,7 +156,13 @@ stencil_status_t stencil_plan_describe(stencil_plan_t plan, char *buf, int32_t l
 /* u_out := T Jacobi steps applied to u_in (Section 1; fused per Section 3.3).
  * Both are device pointers of the plan's shape and dtype; u_in is only read;
  * u_out must not overlap u_in.  T = 0 copies.  Intermediate passes use a
- * plan-owned device buffer of one grid, allocated on first use. */
+ * plan-owned device buffer of one grid; the persistent launch also keeps a
+ * small block of per-tile counters.  Both are allocated on first use (and the
+ * counters regrown when a new k or tile length needs more), so a call that is
+ * to be captured into a CUDA graph should follow one uncaptured call with the
+ * same settings.  Asynchronous on `stream`; a device-side timeout is read
+ * with stencil_get_device_status.  Plans are not safe for concurrent use on
+ * several streams. */
 stencil_status_t stencil_run(stencil_plan_t plan, const void *u_in, void *u_out, int64_t T, void *stream);
 
 /* Same computation on HOST buffers: copies h_in to the device, runs T steps,
