@@ -114,14 +114,14 @@ static stencil_status_t cuda_fail(cudaError_t e, const char *what) {
     return STENCIL_ERR_CUDA;
 }
 
-// 32 bytes: the status word at offset 0, two job-ticket counters at 16
+// 32 bytes: the status word at offset 0, the per-pass kernels' job tickets at 16
 static stencil_status_t ensure_status_word(stencil_plan_s *P) {
     if (P->d_status) return STENCIL_OK;
     cudaError_t e = cudaMalloc(&P->d_status, 32);
     if (e != cudaSuccess) { P->d_status = nullptr; set_error("status word allocation failed"); return STENCIL_ERR_OOM; }
     e = cudaMemset(P->d_status, 0, 32);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
-    P->d_ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(P->d_status) + 16);
+    P->d_ctr = reinterpret_cast<char *>(P->d_status) + 16;
     return STENCIL_OK;
 }
 
@@ -132,7 +132,7 @@ cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t
         P.d_mp = nullptr;
         P.mp_tiles_cap = 0;
     }
-    const size_t bytes = 2 * kMpCtlBytes + 2 * sizeof(int) * (size_t)tiles;
+    const size_t bytes = kMpCtlBytes + sizeof(int) * (size_t)tiles;
     cudaError_t e = cudaMalloc(&P.d_mp, bytes);
     if (e != cudaSuccess) {
         P.d_mp = nullptr;
@@ -141,7 +141,6 @@ cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t
     e = cudaMemsetAsync(P.d_mp, 0, bytes, st);
     if (e != cudaSuccess) return e;
     P.mp_tiles_cap = tiles;
-    P.mp_seq = 0;
     return cudaSuccess;
 }
 

@@ -199,6 +199,27 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
     return v;
 }
 
+// Job tickets of the one-launch-per-pass kernels (16 bytes of the plan's
+// status block).
+struct JobCtl {
+    unsigned long long ticket;
+    unsigned exited;   // workers (warps or CTAs) that have left the launch
+    unsigned pad;
+};
+static_assert(sizeof(JobCtl) == 16, "job tickets occupy 16 bytes of the plan's status block");
+
+// A launch leaves its counters clean for the next launch -- also when a
+// captured CUDA graph replays the same launch with the same parameters:
+// every worker counts itself out after its last access, and the one that
+// finds itself last (true here) resets what the launch used.  Called by one
+// thread per worker.
+__device__ __forceinline__ bool worker_exit_is_last(unsigned *exited, unsigned workers) {
+    __threadfence();
+    const bool last = atomicAdd(exited, 1u) == workers - 1;
+    if (last) __threadfence();
+    return last;
+}
+
 // *ctr += v with release semantics at GPU scope: this thread's earlier
 // accesses (and those it has observed, e.g. through __syncwarp) are visible
 // to any thread that acquires the new value

@@ -164,9 +164,8 @@ template <typename C> struct F1MpParams {
     int cpj, tiles;         // output chunks per tile, tiles
     int vec_ok;
     int *status;
-    MpCtl *ctl;             // [2]; this launch uses ctl[parity], clears ctl[parity ^ 1]
-    int *done;              // [2][cap]: passes each tile has finished
-    int cap, parity;
+    MpCtl *ctl;             // ticket, abort flag, exit count
+    int *done;              // [tiles]: passes each tile has finished (all left at zero by the last warp)
     const int *skip;        // test hook: the item whose completion is never published (null: none)
     C w[7];
 };
@@ -184,16 +183,8 @@ __global__ void __launch_bounds__(F1_NW * 32) fused1d_mp_kernel(const __grid_con
     using C = typename Traits<DT>::C;
     constexpr int CW = 32 * Traits<DT>::V;
     const int lane = threadIdx.x & 31;
-    {
-        int *other = p.done + (size_t)(p.parity ^ 1) * p.cap;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.cap; i += gridDim.x * blockDim.x) other[i] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            p.ctl[p.parity ^ 1].ticket = 0ull;
-            p.ctl[p.parity ^ 1].abort = 0;
-        }
-    }
-    MpCtl *ctl = p.ctl + p.parity;
-    int *done = p.done + (size_t)p.parity * p.cap;
+    MpCtl *ctl = p.ctl;
+    int *done = p.done;
     C wr[2 * R + 1];
 #pragma unroll
     for (int j = 0; j < 2 * R + 1; ++j) wr[j] = p.w[j];
@@ -224,7 +215,7 @@ __global__ void __launch_bounds__(F1_NW * 32) fused1d_mp_kernel(const __grid_con
                     atomicExch(&ctl->abort, 1);
                     record_status(p.status, kStatusTimeout);
                 }
-                return;
+                break;
             }
             __syncwarp();   // every lane's acquire precedes every lane's (L2) reads
         }
@@ -234,6 +225,18 @@ __global__ void __launch_bounds__(F1_NW * 32) fused1d_mp_kernel(const __grid_con
         fused1d_job<DT, R, K, true>(src, dst, n, periodic, p.g.bval, wr, c0, c1, p.vec_ok != 0, lane);
         __syncwarp();
         if (lane == 0 && !(p.skip && *p.skip == (long long)t)) red_release_add(&done[j], 1);
+    }
+    // the last warp out leaves the counters at zero for the next launch
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = worker_exit_is_last(&ctl->exited, gridDim.x * F1_NW);
+    if (__shfl_sync(0xffffffffu, last, 0)) {
+        for (int i = lane; i < p.tiles; i += 32) done[i] = 0;
+        if (lane == 0) {
+            ctl->ticket = 0ull;
+            ctl->abort = 0;
+            ctl->exited = 0u;
+        }
     }
 }
 
@@ -295,9 +298,7 @@ static cudaError_t launch_f1mp_t(const stencil_plan_s &P, const void *src0, void
     cudaError_t e = ensure_mp_state(P, p.tiles, st);
     if (e != cudaSuccess) return e;
     p.ctl = static_cast<MpCtl *>(P.d_mp);
-    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
-    p.cap = (int)P.mp_tiles_cap;
-    p.parity = (int)(P.mp_seq++ & 1u);
+    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
     // warps for about two passes of tiles: more would take tickets many
     // passes ahead and only poll their dependencies
     const int64_t jobs = std::min<int64_t>((int64_t)p.tiles * passes, 2 * (int64_t)p.tiles);

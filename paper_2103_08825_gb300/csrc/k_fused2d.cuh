@@ -66,17 +66,16 @@ template <typename C> struct F2Params {
     int64_t Ly;
     int vec_ok;        // rows and both base pointers allow V-wide vector access
     int *status;
-    unsigned long long *ctr;   // job tickets: this launch uses ctr[parity], resets the other
-    int parity;
+    JobCtl *ctl;       // job tickets (left at zero by the launch's last warp)
     C w[25];           // evaluation order; up to the r = 2 box
 };
 
-// Control block of a persistent multi-pass launch: the item ticket and the
-// abort flag raised when a dependency wait gives up.
+// Control block of a persistent multi-pass launch: the item ticket, the
+// abort flag raised when a dependency wait gives up, and the exit count.
 struct MpCtl {
     unsigned long long ticket;
     int abort;
-    int pad;
+    unsigned exited;
 };
 
 static_assert(sizeof(MpCtl) == kMpCtlBytes, "control block layout");
@@ -90,11 +89,9 @@ template <typename C> struct F2MpParams {
     int bands, chunks, Ly;
     int vec_ok;
     int *status;
-    MpCtl *ctl;        // [2]; this launch uses ctl[parity], clears ctl[parity ^ 1]
-    int *done;         // [2][cap]: passes each tile has finished (same parity rule;
-                       // the whole other half is cleared, whatever its next tiling)
-    int tiles, cap;
-    int parity;
+    MpCtl *ctl;        // ticket, abort flag, exit count
+    int *done;         // [tiles]: passes each tile has finished
+    int tiles;         // (all left at zero by the launch's last warp)
     const int *skip;   // test hook: the item whose completion is never published (null: none)
     C w[25];
 };
@@ -436,12 +433,11 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     const C *wr = p.w;   // parameter space: FMAs can read the weights as constant operands
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
     uint32_t gst = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = 0ull;   // for the next launch
     // jobs are taken dynamically, so faster SMs take more; the first and last
     // row chunks (Dirichlet edges, the slower jobs) come first
     for (;;) {
         unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&p.ctr[p.parity], 1ull);
+        if (lane == 0) t = atomicAdd(&p.ctl->ticket, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= (unsigned long long)p.jobs) break;
         const int64_t band = (int64_t)(t % p.bands), tc = (int64_t)(t / p.bands);
@@ -463,8 +459,13 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
                                                            p.vec_ok != 0, stg, bars, gst, lane);
         if (!ok) {
             if (lane == 0) record_status(p.status, kStatusTimeout);
-            return;
+            break;
         }
+    }
+    __syncwarp();
+    if (lane == 0 && worker_exit_is_last(&p.ctl->exited, gridDim.x * F2_NW)) {
+        p.ctl->ticket = 0ull;
+        p.ctl->exited = 0u;
     }
 }
 
@@ -502,17 +503,8 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
         }
         __syncwarp();
     }
-    // clear the other parity's counters for the next launch (stream-ordered)
-    {
-        int *other = p.done + (size_t)(p.parity ^ 1) * p.cap;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.cap; i += gridDim.x * blockDim.x) other[i] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            p.ctl[p.parity ^ 1].ticket = 0ull;
-            p.ctl[p.parity ^ 1].abort = 0;
-        }
-    }
-    MpCtl *ctl = p.ctl + p.parity;
-    int *done = p.done + (size_t)p.parity * p.cap;
+    MpCtl *ctl = p.ctl;
+    int *done = p.done;
     const C *wr = p.w;
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
     const int nx = (int)p.g.n2, ny = (int)p.g.n1;
@@ -552,7 +544,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
                     atomicExch(&ctl->abort, 1);
                     record_status(p.status, kStatusTimeout);
                 }
-                return;
+                break;
             }
             // every lane's acquire precedes every lane's reads; TMA reads
             // (async proxy) also need the proxy fence
@@ -577,13 +569,25 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
                 atomicExch(&ctl->abort, 1);
                 record_status(p.status, kStatusTimeout);
             }
-            return;
+            break;
         }
         // publish: every lane's stores, then (release) the tile's pass count
         __syncwarp();
         if (lane == 0 && !(p.skip && *p.skip == (long long)t)) {
             if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
+        }
+    }
+    // the last warp out leaves the counters at zero for the next launch
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = worker_exit_is_last(&ctl->exited, gridDim.x * F2_NW);
+    if (__shfl_sync(0xffffffffu, last, 0)) {
+        for (int i = lane; i < p.tiles; i += 32) done[i] = 0;
+        if (lane == 0) {
+            ctl->ticket = 0ull;
+            ctl->abort = 0;
+            ctl->exited = 0u;
         }
     }
 }
@@ -631,8 +635,7 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.src = src;
     p.dst = dst;
     p.status = P.d_status;
-    p.ctr = P.d_ctr;
-    p.parity = (int)(P.job_seq++ & 1u);
+    p.ctl = static_cast<JobCtl *>(P.d_ctr);
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1];
     if (ny + 4 * R * K + 64 >= (1ll << 31)) return cudaErrorNotSupported;   // rows are 32-bit in the kernel
@@ -725,9 +728,7 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     e = ensure_mp_state(P, p.tiles, st);
     if (e != cudaSuccess) return e;
     p.ctl = static_cast<MpCtl *>(P.d_mp);
-    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
-    p.cap = (int)P.mp_tiles_cap;
-    p.parity = (int)(P.mp_seq++ & 1u);
+    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
     p.skip = P.d_skip;
     const int64_t jobs = (int64_t)p.tiles * passes;
     int64_t grid = (jobs + F2_NW - 1) / F2_NW;

@@ -65,8 +65,7 @@ template <typename C> struct F3Params {
     int64_t jobs, tiles_x, tiles_y, Lz;
     int vec_ok;
     int *status;
-    unsigned long long *ctr;   // job tickets: this launch uses ctr[parity], resets the other
-    int parity;
+    JobCtl *ctl;            // job tickets (left at zero by the launch's last CTA)
     C w[125];               // evaluation order; up to the r = 2 box
 };
 
@@ -79,10 +78,9 @@ template <typename C> struct F3MpParams {
     int tiles_x, tiles_y, chunks, Lz;
     int vec_ok;
     int *status;
-    MpCtl *ctl;             // [2]; this launch uses ctl[parity], clears ctl[parity ^ 1]
-    int *done;              // [2][cap]: passes each tile has finished
-    int tiles, cap;
-    int parity;
+    MpCtl *ctl;             // ticket, abort flag, exit count
+    int *done;              // [tiles]: passes each tile has finished
+    int tiles;              // (all left at zero by the launch's last CTA)
     const int *skip;        // test hook: the item whose completion is never published (null: none)
     C w[125];
 };
@@ -490,12 +488,11 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     uint32_t gst = 0;   // planes consumed so far by this CTA (stage ring position)
     int xpar = 0;       // exchange-buffer parity
     __shared__ unsigned long long s_ticket;
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = 0ull;   // for the next launch
     // jobs are taken dynamically (faster SMs take more); the first and last z
     // ranges (Dirichlet edges) come first
     const int64_t nch = p.jobs / (p.tiles_x * p.tiles_y);
     for (;;) {
-        if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctr[p.parity], 1ull);
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctl->ticket, 1ull);
         __syncthreads();
         const unsigned long long t = s_ticket;
         __syncthreads();
@@ -518,8 +515,13 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
                                                     stages, xbuf, bars, gst, xpar, lane, warp);
         if (!ok) {
             if (threadIdx.x == 0) record_status(p.status, kStatusTimeout);
-            return;
+            break;
         }
+    }
+    // (the job loop's exits are uniform across the CTA)
+    if (threadIdx.x == 0 && worker_exit_is_last(&p.ctl->exited, gridDim.x)) {
+        p.ctl->ticket = 0ull;
+        p.ctl->exited = 0u;
     }
 }
 
@@ -555,18 +557,9 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             prefetch_tmap(&tm_odd);
         }
     }
-    // clear the other parity's counters for the next launch (stream-ordered)
-    {
-        int *other = p.done + (size_t)(p.parity ^ 1) * p.cap;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.cap; i += gridDim.x * blockDim.x) other[i] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            p.ctl[p.parity ^ 1].ticket = 0ull;
-            p.ctl[p.parity ^ 1].abort = 0;
-        }
-    }
     __syncthreads();
-    MpCtl *ctl = p.ctl + p.parity;
-    int *done = p.done + (size_t)p.parity * p.cap;
+    MpCtl *ctl = p.ctl;
+    int *done = p.done;
     C wr[Sh::npts];
 #pragma unroll
     for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
@@ -618,7 +611,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
                     atomicExch(&ctl->abort, 1);
                     record_status(p.status, kStatusTimeout);
                 }
-                return;
+                break;
             }
             if constexpr (PROD == PROD3_TMA) {
                 if (threadIdx.x == 0) fence_proxy_async_global();
@@ -640,12 +633,26 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
                 atomicExch(&ctl->abort, 1);
                 record_status(p.status, kStatusTimeout);
             }
-            return;
+            break;
         }
         // fused3d_job ends with a barrier after the CTA's last stores: publish
         if (threadIdx.x == 0 && !(p.skip && *p.skip == (long long)t)) {
             if constexpr (PROD == PROD3_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
+        }
+    }
+    // the last CTA out leaves the counters at zero for the next launch (the
+    // loop's exits are uniform across the CTA)
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = worker_exit_is_last(&ctl->exited, gridDim.x);
+    __syncthreads();
+    if (s_last) {
+        for (int i = threadIdx.x; i < p.tiles; i += F3_THREADS) done[i] = 0;
+        if (threadIdx.x == 0) {
+            ctl->ticket = 0ull;
+            ctl->abort = 0;
+            ctl->exited = 0u;
         }
     }
 }
@@ -676,8 +683,7 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.src = src;
     p.dst = dst;
     p.status = P.d_status;
-    p.ctr = P.d_ctr;
-    p.parity = (int)(P.job_seq++ & 1u);
+    p.ctl = static_cast<JobCtl *>(P.d_ctr);
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
     p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
@@ -775,9 +781,7 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     e = ensure_mp_state(P, tiles, st);
     if (e != cudaSuccess) return e;
     p.ctl = static_cast<MpCtl *>(P.d_mp);
-    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + 2 * sizeof(MpCtl));
-    p.cap = (int)P.mp_tiles_cap;
-    p.parity = (int)(P.mp_seq++ & 1u);
+    p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
     p.skip = P.d_skip;
     const int64_t jobs = tiles * passes;
     const int64_t grid = jobs < slots ? jobs : slots;

@@ -12,7 +12,7 @@
 
 namespace sg {
 constexpr int kHostMaxPts = 343;
-constexpr size_t kMpCtlBytes = 16;   // one control block of a persistent multi-pass launch
+constexpr size_t kMpCtlBytes = 16;   // the control block of a persistent multi-pass launch
 }
 
 struct stencil_plan_s {
@@ -35,13 +35,11 @@ struct stencil_plan_s {
     void *hws[2] = {nullptr, nullptr};   // device copies for stencil_run_host
     size_t grid_bytes = 0;
     int *d_status = nullptr;   // device status word (0 = OK)
-    unsigned long long *d_ctr = nullptr;   // two job-ticket counters (same allocation)
-    mutable unsigned job_seq = 0;          // launches that used the counters
-    // persistent multi-pass launches: two control blocks, then two per-tile
-    // pass counters; a launch uses one parity and clears the other
+    void *d_ctr = nullptr;     // job tickets of the per-pass kernels (sg::JobCtl, same allocation)
+    // persistent multi-pass launches: a control block, then one pass counter
+    // per tile; every launch leaves them at zero
     mutable void *d_mp = nullptr;
     mutable int64_t mp_tiles_cap = 0;
-    mutable unsigned mp_seq = 0;
     int *d_skip = nullptr;     // test hook: a persistent-launch item that never publishes (null unless set)
     // adjoint workspace
     void *adj_ws = nullptr;

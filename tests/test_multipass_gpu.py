@@ -302,3 +302,38 @@ def test_1d_int32_bit_exact_and_fp64_identical(r, bkind, n):
     for cpj in (1, 13, 40):
         sg.stencil_plan_set_tile_rows(pf, cpj)
         assert torch.equal(run(pf, xf, T, 4, FUSED), plain), f"cpj={cpj}"
+
+
+
+@pytest.mark.parametrize("variant", [FUSED, PER_PASS])
+def test_cuda_graph_replay(variant):
+    """stencil_run captured into a CUDA graph (after one uncaptured call with
+    the same settings) and replayed: every launch leaves its ticket and
+    dependency counters at zero, so each replay -- the same parameters --
+    recomputes the result."""
+    sg = sgmod()
+    cases = [(1, (100003,), [0.25, 0.5, 0.25], 21, 4), (2, (700, 1000), [0.5, 0.125, 0.125, 0.125, 0.125], 22, 4),
+             (3, (40, 70, 300), [0.4] + [0.1] * 6, 13, 3)]
+    for dim, shape, w, T, k in cases:
+        plan = sg.stencil_plan_create(dim, 1, shape, STAR, w, DIRICHLET, 0.0, sg.STENCIL_F32)
+        x = torch.rand(shape, device=DEV)
+        plain = run(plan, x, T, 1, PLAIN)
+        sg.stencil_plan_set_variant(plan, variant)
+        sg.stencil_plan_set_k(plan, k)
+        y = torch.empty_like(x)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            sg.stencil_run(plan, x, y, T)          # allocates workspace and counters
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            sg.stencil_run(plan, x, y, T)
+        for _ in range(3):
+            y.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert sg.stencil_get_device_status(plan) == 0
+            assert torch.equal(y, plain), f"dim={dim} variant={variant}"
+        # and an ordinary call afterwards
+        assert torch.equal(run(plan, x, T, k, variant), plain)
