@@ -96,7 +96,7 @@ def load(path: str | None = None):
         "stencil_get_device_status": (st, [vp]),
         "stencil_status_string": (ctypes.c_char_p, [st]),
         "stencil_batch_test_skip_publish": (st, [vp, i64]),
-        "stencil_plan_test_skip_publish": (st, [vp, i64]),
+        "stencil_plan_test_poison_counter": (st, [vp, i64]),
         "stencil_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

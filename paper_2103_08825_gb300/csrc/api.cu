@@ -286,7 +286,6 @@ stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
     cudaFree(P->adj_ws);
     cudaFree(P->adj_partials);
     cudaFree(P->d_mp);
-    cudaFree(P->d_skip);
     cudaSetDevice(cur);
     delete P;
     return STENCIL_OK;
@@ -521,17 +520,18 @@ stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, in
     return STENCIL_OK;
 }
 
-// Test hook (not in the public header): item q of the plan's persistent
-// multi-pass launches skips its completion publish, so that the items that
-// depend on it must give up their bounded waits -- host-side fault injection
-// for the timeout path.  q < 0 disables.
-stencil_status_t stencil_plan_test_skip_publish(stencil_plan_t P, int64_t q) {
-    if (!P) return STENCIL_ERR_INVALID_ARG;
-    if (!P->d_skip) {
-        if (cudaMalloc(&P->d_skip, sizeof(int)) != cudaSuccess) return STENCIL_ERR_OOM;
-    }
-    const int v = q < 0 ? -1 : (int)q;
-    if (cudaMemcpy(P->d_skip, &v, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return STENCIL_ERR_CUDA;
+// Test hook (not in the public header): sets tile `tile`'s pass counter of
+// the plan's persistent multi-pass launches to a large negative value, so that
+// the items of later passes that depend on it must give up their bounded
+// waits -- host-side fault injection for the timeout path.  The launch's last
+// worker resets every counter to zero as usual.  The counters must exist (a
+// persistent launch has run) and no launch of the plan may be in flight.
+stencil_status_t stencil_plan_test_poison_counter(stencil_plan_t P, int64_t tile) {
+    if (!P || tile < 0) return STENCIL_ERR_INVALID_ARG;
+    if (!P->d_mp || tile >= P->mp_tiles_cap) return STENCIL_ERR_INVALID_ARG;
+    const int v = -(1 << 30);
+    int *done = reinterpret_cast<int *>(static_cast<char *>(P->d_mp) + kMpCtlBytes);
+    if (cudaMemcpy(done + tile, &v, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return STENCIL_ERR_CUDA;
     return STENCIL_OK;
 }
 

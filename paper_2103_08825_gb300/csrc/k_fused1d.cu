@@ -166,7 +166,6 @@ template <typename C> struct F1MpParams {
     int *status;
     MpCtl *ctl;             // ticket, abort flag, exit count
     int *done;              // [tiles]: passes each tile has finished (all left at zero by the last warp)
-    const int *skip;        // test hook: the item whose completion is never published (null: none)
     C w[7];
 };
 
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(F1_NW * 32) fused1d_mp_kernel(const __grid_con
         S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
         fused1d_job<DT, R, K, true>(src, dst, n, periodic, p.g.bval, wr, c0, c1, p.vec_ok != 0, lane);
         __syncwarp();
-        if (lane == 0 && !(p.skip && *p.skip == (long long)t)) red_release_add(&done[j], 1);
+        if (lane == 0) red_release_add(&done[j], 1);
     }
     // the last warp out leaves the counters at zero for the next launch
     __syncwarp();
@@ -286,7 +285,6 @@ static cudaError_t launch_f1mp_t(const stencil_plan_s &P, const void *src0, void
     p.dst_odd = dst_odd;
     p.passes = passes;
     p.status = P.d_status;
-    p.skip = P.d_skip;
     for (int j = 0; j < 2 * R + 1; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     p.vec_ok = ((uintptr_t)src0 % 16 == 0) && ((uintptr_t)dst_even % 16 == 0) && ((uintptr_t)dst_odd % 16 == 0);
     const int64_t nchunks = (P.n[2] + CW - 1) / CW;

@@ -92,7 +92,6 @@ template <typename C> struct F2MpParams {
     MpCtl *ctl;        // ticket, abort flag, exit count
     int *done;         // [tiles]: passes each tile has finished
     int tiles;         // (all left at zero by the launch's last warp)
-    const int *skip;   // test hook: the item whose completion is never published (null: none)
     C w[25];
 };
 
@@ -573,7 +572,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
         }
         // publish: every lane's stores, then (release) the tile's pass count
         __syncwarp();
-        if (lane == 0 && !(p.skip && *p.skip == (long long)t)) {
+        if (lane == 0) {
             if constexpr (PROD == PROD_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
         }
@@ -729,7 +728,6 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     if (e != cudaSuccess) return e;
     p.ctl = static_cast<MpCtl *>(P.d_mp);
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
-    p.skip = P.d_skip;
     const int64_t jobs = (int64_t)p.tiles * passes;
     int64_t grid = (jobs + F2_NW - 1) / F2_NW;
     if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;

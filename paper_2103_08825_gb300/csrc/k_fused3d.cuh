@@ -81,7 +81,6 @@ template <typename C> struct F3MpParams {
     MpCtl *ctl;             // ticket, abort flag, exit count
     int *done;              // [tiles]: passes each tile has finished
     int tiles;              // (all left at zero by the launch's last CTA)
-    const int *skip;        // test hook: the item whose completion is never published (null: none)
     C w[125];
 };
 
@@ -636,7 +635,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             break;
         }
         // fused3d_job ends with a barrier after the CTA's last stores: publish
-        if (threadIdx.x == 0 && !(p.skip && *p.skip == (long long)t)) {
+        if (threadIdx.x == 0) {
             if constexpr (PROD == PROD3_TMA) fence_proxy_async_global();
             red_release_add(&done[j], 1);
         }
@@ -782,7 +781,6 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     if (e != cudaSuccess) return e;
     p.ctl = static_cast<MpCtl *>(P.d_mp);
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
-    p.skip = P.d_skip;
     const int64_t jobs = tiles * passes;
     const int64_t grid = jobs < slots ? jobs : slots;
     kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(maps[0], maps[1], maps[2], p);

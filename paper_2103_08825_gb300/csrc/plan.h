@@ -40,7 +40,6 @@ struct stencil_plan_s {
     // per tile; every launch leaves them at zero
     mutable void *d_mp = nullptr;
     mutable int64_t mp_tiles_cap = 0;
-    int *d_skip = nullptr;     // test hook: a persistent-launch item that never publishes (null unless set)
     // adjoint workspace
     void *adj_ws = nullptr;
     size_t adj_ws_bytes = 0;

@@ -247,11 +247,11 @@ def test_3d_bench_size_sampled():
 
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_dependency_timeout_is_reported_and_recovers(dim):
-    """Host-side fault injection: one tile of pass 0 never publishes its
-    completion, so the tiles of pass 1 that read it must give up their bounded
-    waits (about one second), raise the abort flag and report
-    STENCIL_ERR_TIMEOUT; the context stays usable and the next run (the
-    other counter parity, cleared by the aborted launch) is correct."""
+    """Host-side fault injection: tile 0's pass counter is poisoned (a large
+    negative value), so the tiles of pass 1 that read it must give up their
+    bounded waits (about one second), raise the abort flag and report
+    STENCIL_ERR_TIMEOUT; the context stays usable, the aborted launch's last
+    worker resets the counters, and the next runs are correct."""
     import time
     sg = sgmod()
     shape = {1: (100003,), 2: (300, 500), 3: (40, 70, 300)}[dim]
@@ -261,13 +261,15 @@ def test_dependency_timeout_is_reported_and_recovers(dim):
     plain = run(plan, x, 8, 1, PLAIN)
     sg.stencil_plan_set_variant(plan, FUSED)
     sg.stencil_plan_set_k(plan, 2)
-    assert sg.load().stencil_plan_test_skip_publish(plan.handle, 0) == 0
     y = torch.empty_like(x)
+    sg.stencil_run(plan, x, y, 8)            # allocates the counters
+    torch.cuda.synchronize()
+    assert sg.stencil_get_device_status(plan) == 0
+    assert sg.load().stencil_plan_test_poison_counter(plan.handle, 0) == 0
     t0 = time.time()
     sg.stencil_run(plan, x, y, 8)
     assert sg.stencil_get_device_status(plan) == sg.STENCIL_ERR_TIMEOUT
     assert time.time() - t0 < 30
-    assert sg.load().stencil_plan_test_skip_publish(plan.handle, -1) == 0
     for _ in range(2):
         assert torch.equal(run(plan, x, 8, 2, FUSED), plain)
 
