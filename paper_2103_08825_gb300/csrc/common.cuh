@@ -255,16 +255,26 @@ __device__ __forceinline__ bool wait_counter(const int *ctr, int target, const i
 // hi <= 2n.
 struct TileSpan {
     int a0, n0, a1, n1, a2, n2;
-    __device__ __forceinline__ int count() const { return n0 + n1 + n2; }
-    __device__ __forceinline__ int at(int i) const { return i < n0 ? a0 + i : i < n0 + n1 ? a1 + i - n0 : a2 + i - n0 - n1; }
+    __host__ __device__ __forceinline__ int count() const { return n0 + n1 + n2; }
+    __host__ __device__ __forceinline__ int at(int i) const {
+        return i < n0 ? a0 + i : i < n0 + n1 ? a1 + i - n0 : a2 + i - n0 - n1;
+    }
 };
 
-__device__ __forceinline__ TileSpan tile_span(int lo, int hi, int n, int len, bool periodic) {
+__host__ __device__ __forceinline__ TileSpan tile_span(int lo, int hi, int n, int len, bool periodic) {
     TileSpan s{0, 0, 0, 0, 0, 0};
     const int c0 = lo > 0 ? lo : 0, c1 = hi < n ? hi : n;
     if (c0 < c1) { s.a0 = c0 / len; s.n0 = (c1 - 1) / len + 1 - s.a0; }
-    if (periodic && lo < 0) { s.a1 = (lo + n) / len; s.n1 = (n - 1) / len + 1 - s.a1; }
-    if (periodic && hi > n) { s.a2 = 0; s.n2 = (hi - n - 1) / len + 1; }
+    if (periodic && lo < 0) {   // [lo, min(hi, 0)) wrapped up by n
+        const int w1 = (hi < 0 ? hi : 0) + n;
+        s.a1 = (lo + n) / len;
+        s.n1 = (w1 - 1) / len + 1 - s.a1;
+    }
+    if (periodic && hi > n) {   // [max(lo, n), hi) wrapped down by n
+        const int w0 = (lo > n ? lo : n) - n;
+        s.a2 = w0 / len;
+        s.n2 = (hi - n - 1) / len + 1 - s.a2;
+    }
     return s;
 }
 

@@ -1,0 +1,29 @@
+"""Host-side logic of the CUDA library that needs no GPU: the dependency sets
+of the persistent multi-pass kernels (tile_span in common.cuh), compiled by
+nvcc as host code and checked against brute force."""
+
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2103_08825_gb300", "csrc")
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and os.path.exists(c):
+            return c
+    pytest.skip("nvcc not available")
+
+
+def test_tile_span_matches_brute_force(tmp_path):
+    exe = tmp_path / "tile_span_check"
+    src = os.path.join(ROOT, "tests", "host", "tile_span_check.cu")
+    subprocess.run([_nvcc(), "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), src, "-o",
+                    str(exe)], check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok ")
