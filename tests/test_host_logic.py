@@ -1,6 +1,8 @@
-"""Host-side logic of the CUDA library that needs no GPU: the dependency sets
-of the persistent multi-pass kernels (tile_span in common.cuh), compiled by
-nvcc as host code and checked against brute force."""
+"""Host-side logic of the CUDA library that needs no GPU, compiled by nvcc as
+host code: the dependency sets of the persistent multi-pass kernels
+(tile_span in common.cuh) against brute force, and the tile geometry of the
+fused kernels (f2_tiling, f3_lz) against its covering and minimum-length
+rules."""
 
 import os
 import shutil
@@ -24,6 +26,17 @@ def test_tile_span_matches_brute_force(tmp_path):
     src = os.path.join(ROOT, "tests", "host", "tile_span_check.cu")
     subprocess.run([_nvcc(), "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), src, "-o",
                     str(exe)], check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok ")
+
+
+def test_tile_geometry_covers_each_axis(tmp_path):
+    exe = tmp_path / "tiling_check"
+    src = os.path.join(ROOT, "tests", "host", "tiling_check.cu")
+    subprocess.run([_nvcc(), "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "--expt-relaxed-constexpr", "-I", CSRC, "-I", os.path.join(ROOT, "include"), src, "-o", str(exe)],
+                   check=True, capture_output=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok ")
