@@ -173,6 +173,12 @@ stencil_status_t stencil_run_host(stencil_plan_t plan, const void *h_in, void *h
 
 /* ---------------------------------------------------------------- batches */
 
+/* The paper has no batched form: its experiments advance one grid at a time
+ * (Section 4).  This entry point serves the batched workload of this
+ * library's specification (256 periodic 2D 9-point grids of uneven sizes and
+ * step counts in one persistent, graph-captured launch); each member's result
+ * is the Section 1 sweep of that member. */
+
 /* A batch of `n` independent 2D grids of one dtype, order and boundary, each
  * with its own shape (shapes: n x dim, outermost first), coefficients
  * (weights[i]) and step count (T[i] >= 0).  All grids are advanced together
@@ -198,6 +204,11 @@ stencil_status_t stencil_batch_launch_count(stencil_batch_t batch, int64_t *laun
 
 /* ----------------------------------------------------------------- adjoint */
 
+/* The paper does not differentiate the sweep.  This entry point serves the
+ * differentiation workload of this library's specification (gradients of a
+ * loss of u_T with respect to u_0 and the weights, recomputed from
+ * checkpoints); the forward map it differentiates is the Section 1 sweep. */
+
 /* Reverse-mode derivative of u_T = (T steps)(u0) for F32 plans: given
  * grad_uT = dL/du_T (device, plan shape), writes grad_u0 = dL/du0 (device,
  * plan shape) and grad_w[j] = dL/dw_j (device, `count` doubles, compact
@@ -210,6 +221,9 @@ stencil_status_t stencil_adjoint_run(stencil_plan_t plan, const void *u0, const 
                                      int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream);
 
 /* -------------------------------------------------------------- reductions */
+
+/* Not in the paper: the FP64 conservation and norm reductions of this
+ * library's specification (mass, squared norm, the adjoint workload's loss). */
 
 typedef enum {
     STENCIL_REDUCE_SUM = 0,       /* sum u                       */
@@ -230,17 +244,17 @@ stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void *u, const v
  * memory pools (stencil_reduce takes its partial-sum buffer with
  * cudaMallocAsync), applications whose caching allocator already holds nearly
  * all free device memory, and latency-critical loops that must not enter an
- * allocator.  Same arguments, same summation order and so the same result as
- * stencil_reduce, but the per-block partial sums live in a library-static
- * device array of 1024 doubles (8 KiB), which every GPU that loads the
- * library holds until the process exits; no cudaMalloc, cudaMallocAsync,
- * cudaFree or other allocating call is made.  The reduction never uses more
- * than 1024 partial sums, so n is not limited by the array; a call whose
- * partition needed more would return STENCIL_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  Every call reuses the same array
- * (each call writes every partial it reads, so nothing needs clearing):
+ * allocator.  Same arguments, same partition and summation order and so a
+ * bit-identical result to stencil_reduce, but the per-block partial sums live
+ * in a library-static device array of 1024 doubles (8 KiB), which every GPU
+ * that loads the library holds until the process exits; no cudaMalloc,
+ * cudaMallocAsync, cudaFree or other allocating call is made.  The reduction
+ * never uses more than 1024 partial sums, so n is not limited by the array.
+ * The first call on a device (and the first after that device's context was
+ * re-created, e.g. by cudaDeviceReset) looks up the array's device address
+ * with cudaGetSymbolAddress, with that device current, and caches it; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array (each call writes every partial it reads, so nothing needs clearing):
  * calls whose kernels overlap on the GPU -- on different streams without
  * ordering between them -- race and can return wrong sums.
  * The paper has no counterpart to this entry point. */

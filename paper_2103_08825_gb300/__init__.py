@@ -254,14 +254,39 @@ def stencil_get_device_status(plan: Plan) -> int:
     return int(load().stencil_get_device_status(plan.handle))
 
 
+def _reduce_args(u, op: int, target, out, what: str):
+    """Host-side checks shared by the reduction wrappers: every pointer the C
+    call receives must be a contiguous tensor of the right dtype, size and
+    device, so that the kernels never read past a buffer or across GPUs."""
+    import torch
+    if not isinstance(u, torch.Tensor) or not u.is_cuda or not u.is_contiguous():
+        raise ValueError(f"{what}: u must be a contiguous CUDA tensor")
+    if u.numel() < 1:
+        raise ValueError(f"{what}: u must not be empty")
+    if int(op) == STENCIL_REDUCE_HALF_SQDIST:
+        if target is None:
+            raise ValueError(f"{what}: HALF_SQDIST needs a target")
+    if target is not None:
+        if not isinstance(target, torch.Tensor) or not target.is_cuda or not target.is_contiguous():
+            raise ValueError(f"{what}: target must be a contiguous CUDA tensor")
+        if target.dtype != u.dtype or target.numel() != u.numel() or target.device != u.device:
+            raise ValueError(f"{what}: target must have u's dtype, number of elements and device")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+    elif (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or out.device != u.device
+          or out.numel() < 1 or not out.is_contiguous()):
+        raise ValueError(f"{what}: out must be a contiguous float64 tensor on u's device")
+    tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
+    return out, tp
+
+
 def stencil_reduce(u, op: int, target=None, out=None, stream=None):
     """FP64 reduction of a CUDA tensor; returns the 1-element float64 CUDA tensor."""
     import torch
-    if out is None:
-        out = torch.empty(1, dtype=torch.float64, device=u.device)
-    tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
-    _check(load().stencil_reduce(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
-                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "stencil_reduce")
+    out, tp = _reduce_args(u, op, target, out, "stencil_reduce")
+    with torch.cuda.device(u.device):
+        _check(load().stencil_reduce(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "stencil_reduce")
     return out
 
 
@@ -270,12 +295,11 @@ def stencil_reduce_noalloc(u, op: int, target=None, out=None, stream=None):
     library-static array); `out` defaults to a new 1-element float64 tensor,
     which the caller may preallocate to avoid torch's allocator as well."""
     import torch
-    if out is None:
-        out = torch.empty(1, dtype=torch.float64, device=u.device)
-    tp = ctypes.c_void_p(target.data_ptr()) if target is not None else ctypes.c_void_p(0)
-    _check(load().stencil_reduce_noalloc(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp, int(op),
-                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
-           "stencil_reduce_noalloc")
+    out, tp = _reduce_args(u, op, target, out, "stencil_reduce_noalloc")
+    with torch.cuda.device(u.device):
+        _check(load().stencil_reduce_noalloc(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp,
+                                             int(op), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "stencil_reduce_noalloc")
     return out
 
 

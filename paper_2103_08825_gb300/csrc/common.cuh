@@ -161,6 +161,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Wait for a copy this CTA issued before it gives up and leaves: the shared
+// memory a bulk copy targets must outlive the copy.  Up to about ten seconds
+// (ten bounded waits); false if the copy still had not landed.
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < 10; ++i)
+        if (mbar_wait_bounded(bar, parity)) return true;
+    return false;
+}
+
 // 2D / 3D tiled TMA loads (global -> shared), completion on an mbarrier.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(

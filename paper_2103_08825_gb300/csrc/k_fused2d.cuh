@@ -284,11 +284,13 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
             if ((i0 & (F2_ROWS - 1)) == 0) {
                 const bool ok = mbar_wait_bounded(&bars[slot], par);
                 if (__any_sync(0xffffffffu, !ok)) {
-                    // give up: wait (bounded) for this warp's copies in flight
+                    // give up: wait (bounded, about ten seconds per stage) for
+                    // this warp's copies in flight before its shared memory can
+                    // be left; the caller records the timeout either way
                     if (lane == 0)
                         for (int qq = q; qq < nst && qq < q + F2_STAGES; ++qq) {
                             const uint32_t gg = gst + qq;
-                            mbar_wait_bounded(&bars[gg % F2_STAGES], (gg / F2_STAGES) & 1u);
+                            if (!mbar_drain(&bars[gg % F2_STAGES], (gg / F2_STAGES) & 1u)) break;
                         }
                     __syncwarp();
                     return false;

@@ -240,6 +240,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                 for (int v = 0; v < V; ++v) P[s][m][j][v] = C(0);
 
     bool bad = false;
+    int ibad = 0;   // the plane whose stage a bounded wait gave up on
     for (int i0 = 0; i0 < nsp; i0 += U) {
 #pragma unroll
         for (int ph = 0; ph < U; ++ph) {
@@ -249,7 +250,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
             // ---- A: stage of plane zin ready
             if constexpr (PROD == PROD3_TMA) {
                 const bool ok = mbar_wait_bounded(&bars[slot], ((gst + i) / F3_STAGES) & 1u);
-                if (__syncthreads_or(!ok)) { bad = true; break; }
+                if (__syncthreads_or(!ok)) { bad = true; ibad = i; break; }
             } else {
                 cp_async_wait<F3_STAGES - 2>();
                 __syncthreads();
@@ -444,10 +445,12 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
     }
     if (bad) {
         if (threadIdx.x == 0) {
-            // wait (bounded) for this CTA's copies still in flight
-            for (int q = 0; q < F3_STAGES; ++q) {
+            // wait (bounded, about ten seconds per stage) for this CTA's
+            // copies still in flight before its shared memory can be left
+            // (the planes ibad .. ibad + F3_STAGES - 1 of the job were issued)
+            for (int q = ibad; q < ibad + F3_STAGES && q < nsp; ++q) {
                 const uint32_t g = gst + q;
-                mbar_wait_bounded(&bars[g % F3_STAGES], (g / F3_STAGES) & 1u);
+                if (!mbar_drain(&bars[g % F3_STAGES], (g / F3_STAGES) & 1u)) break;
             }
         }
         __syncthreads();

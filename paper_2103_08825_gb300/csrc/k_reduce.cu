@@ -83,7 +83,7 @@ static cudaError_t reduce_launch_t(int64_t n, const void *u, const void *tg, int
 int reduce_blocks(int64_t n) {
     int64_t nb = (n + 4095) / 4096;
     if (nb < 1) nb = 1;
-    if (nb > RED_MAX_BLOCKS) nb = RED_MAX_BLOCKS;
+    if (nb > RED_MAX_BLOCKS) nb = RED_MAX_BLOCKS;   // the partial-sum buffers hold RED_MAX_BLOCKS doubles
     return (int)nb;
 }
 
@@ -135,17 +135,41 @@ extern "C" stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void 
 // ------------------------------------------------------------------------
 // Allocation-free variant.  The partial sums of the first pass live in this
 // file-scope device array instead of a stream-ordered allocation.  Its size
-// is the largest number of partials the reduction ever uses (RED_MAX_BLOCKS
-// doubles, 8 KiB), and every GPU that loads the library keeps it until the
-// process exits.  Host code must not hand the array's host-side name to a
-// kernel: the device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// is the largest number of partials the reduction ever uses (reduce_blocks
+// clamps the partition to RED_MAX_BLOCKS, 8 KiB of doubles), and every GPU
+// that loads the library keeps it until the process exits.  Host code must
+// not hand the array's host-side name to a kernel: its device address is
+// looked up with cudaGetSymbolAddress, with the device current, and cached
+// together with the context it belongs to; a call made under another context
+// of the same device (after cudaDeviceReset, say) looks it up again.
 static __device__ __align__(256) double g_reduce_scratch[RED_MAX_BLOCKS];
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-double *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    double *addr;
+    void *ctx;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+typedef int (*CtxGetCurrentFn)(void **);
+
+// The driver's cuCtxGetCurrent, through the runtime's entry-point query (the
+// library does not link libcuda directly).  Null if unavailable.
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
 }  // namespace
 
 extern "C" stencil_status_t stencil_reduce_noalloc(int32_t dtype, int64_t n, const void *u, const void *target,
@@ -159,34 +183,43 @@ extern "C" stencil_status_t stencil_reduce_noalloc(int32_t dtype, int64_t n, con
         set_error("invalid reduction arguments");
         return STENCIL_ERR_INVALID_ARG;
     }
-    const int nb = reduce_blocks(n);
-    if (nb > RED_MAX_BLOCKS) {
-        set_error("stencil_reduce_noalloc: n needs " + std::to_string(nb) + " partial sums, more than the " +
-                  std::to_string(RED_MAX_BLOCKS) + " its static scratch holds");
-        return STENCIL_ERR_INVALID_ARG;
-    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_error("stencil_reduce_noalloc: no usable current device");
         return STENCIL_ERR_CUDA;
     }
+    // make the device's primary context current (CUDA 12 and later initialise
+    // it here; a no-op when it already is), so that the context handle below
+    // names the one the launch will use
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        set_error(std::string("stencil_reduce_noalloc: cudaSetDevice failed: ") + cudaGetErrorString(e));
+        return STENCIL_ERR_CUDA;
+    }
     double *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[dev]) {
-            // first call on this device: find the array's device address
-            e = cudaGetSymbolAddress(reinterpret_cast<void **>(&g_scratch_addr[dev]), g_reduce_scratch);
+        void *ctx = nullptr;
+        if (CtxGetCurrentFn f = ctx_get_current()) f(&ctx);
+        ScratchAddr &s = g_scratch[dev];
+        if (!s.addr || s.ctx != ctx) {
+            // first call on this device (or in a new context): find the array's device address
+            double *a = nullptr;
+            e = cudaGetSymbolAddress(reinterpret_cast<void **>(&a), g_reduce_scratch);
             if (e != cudaSuccess) {
-                g_scratch_addr[dev] = nullptr;
+                s.addr = nullptr;
                 set_error(std::string("stencil_reduce_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
                 return STENCIL_ERR_CUDA;
             }
+            s.addr = a;
+            s.ctx = ctx;
         }
-        scratch = g_scratch_addr[dev];
+        scratch = s.addr;
     }
     // every partial slot the final pass reads is written by the first pass
-    // of the same call, so nothing needs clearing
+    // of the same call (reduce_blocks(n) <= RED_MAX_BLOCKS slots), so nothing
+    // needs clearing
     e = reduce_launch(dtype, n, u, target, op, scratch, out, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         set_error(std::string("reduction launch: ") + cudaGetErrorString(e));

@@ -30,6 +30,11 @@ CASES = [
     (2, 2, STAR, (33, 30), PERIODIC, 0.0, 10, 10),
     (1, 1, STAR, (301,), DIRICHLET, 0.5, 25, 6),
     (1, 2, STAR, (77,), PERIODIC, 0.0, 8, 1),
+    # 3D radius 2, the largest order the adjoint accepts, both patterns
+    (3, 2, STAR, (14, 16, 40), PERIODIC, 0.0, 7, 3),
+    (3, 2, STAR, (12, 15, 22), DIRICHLET, 0.25, 6, 4),
+    (3, 2, BOX, (10, 11, 36), PERIODIC, 0.0, 5, 2),
+    (3, 2, BOX, (9, 12, 13), DIRICHLET, -0.1, 4, 3),
     # extents too small for the row-block kernel: the generic step kernel
     (3, 1, STAR, (3, 4, 5), PERIODIC, 0.0, 5, 2),
     (2, 2, BOX, (5, 6), DIRICHLET, 0.1, 4, 2),
