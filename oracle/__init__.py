@@ -11,7 +11,7 @@ step; Section 3.3 (Algorithm 1) and Section 3.4 reorder these updates without
 changing them.  The conventions the paper leaves open are listed in the header
 of ``oracle.c``.
 
-Pins (all in ``tests/test_oracle_pins.py``): Dirichlet sine eigenmodes,
+Pins (``tests/test_oracle_pins.py``, ``tests/test_oracle_vc_pins.py``): Dirichlet sine eigenmodes,
 periodic Fourier modes, the binomial closed form and its method of images,
 box separability, T-fold self-correlation, mass conservation, dense-matrix
 brute force (FP64 and uint32), the adjoint dot-product identity and finite
@@ -68,6 +68,9 @@ def _load():
         lib.oracle_points_u32.argtypes = [c_int, c_int, c_int, i64p, up, c_int, c_u32, up, c_i64, c_i64, i64p, up]
         lib.oracle_transpose_step_f64.argtypes = [c_int, c_int, c_int, i64p, dp, c_int, dp, dp]
         lib.oracle_adjoint_f64.argtypes = [c_int, c_int, c_int, i64p, dp, c_int, c_dbl, dp, dp, c_i64, dp, dp, dp]
+        lib.oracle_run_vc_f64.argtypes = [c_int, c_int, c_int, i64p, dp, c_int, c_dbl, dp, c_i64, dp]
+        lib.oracle_run_vc_u32.argtypes = [c_int, c_int, c_int, i64p, up, c_int, c_u32, up, c_i64, up]
+        lib.oracle_adjoint_vc_f64.argtypes = [c_int, c_int, c_int, i64p, dp, c_int, c_dbl, dp, dp, c_i64, dp, dp, dp]
         lib.oracle_sum_f64.argtypes = [c_i64, dp, dp]
         lib.oracle_sumsq_f64.argtypes = [c_i64, dp, dp]
         lib.oracle_threads.argtypes = []
@@ -177,6 +180,51 @@ def adjoint(d, r, pattern, shape, w, bkind, bval, u0, target, T):
                                       _p(gu, ctypes.c_double), _p(gw, ctypes.c_double), _p(loss, ctypes.c_double)),
            "adjoint")
     return float(loss[0]), gu, gw
+
+
+def run_vc(d, r, pattern, shape, c, bkind, bval, u0, T) -> np.ndarray:
+    """u_T of the variable-coefficient sweep, FP64; c has shape (npoints,
+    *shape): coefficient field of each compact offset."""
+    n = _shape(shape)
+    N = int(np.prod(shape))
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, N))
+    u0 = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(tuple(shape)))
+    out = np.empty_like(u0)
+    _check(_load().oracle_run_vc_f64(d, r, pattern, _p(n, ctypes.c_int64), _p(c, ctypes.c_double), bkind,
+                                     float(bval), _p(u0, ctypes.c_double), int(T), _p(out, ctypes.c_double)),
+           "run_vc_f64")
+    return out
+
+
+def run_vc_int(d, r, pattern, shape, c, bkind, bval, u0, T) -> np.ndarray:
+    """The variable-coefficient sweep in uint32 wraparound arithmetic (int32 bits)."""
+    n = _shape(shape)
+    N = int(np.prod(shape))
+    cu = np.ascontiguousarray(np.asarray(c).astype(np.int64).astype(np.uint32).reshape(-1, N))
+    u = np.ascontiguousarray(np.asarray(u0).astype(np.int64).astype(np.uint32).reshape(tuple(shape)))
+    out = np.empty_like(u)
+    _check(_load().oracle_run_vc_u32(d, r, pattern, _p(n, ctypes.c_int64), _p(cu, ctypes.c_uint32), bkind,
+                                     int(bval) & 0xFFFFFFFF, _p(u, ctypes.c_uint32), int(T),
+                                     _p(out, ctypes.c_uint32)), "run_vc_u32")
+    return out.view(np.int32)
+
+
+def adjoint_vc(d, r, pattern, shape, c, bkind, bval, u0, target, T):
+    """(loss, grad_u0, grad_c) of loss = 0.5 * ||u_T - target||^2 for the
+    variable-coefficient sweep (grad_c shaped like c)."""
+    n = _shape(shape)
+    N = int(np.prod(shape))
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, N))
+    u0 = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(tuple(shape)))
+    tg = np.ascontiguousarray(np.asarray(target, dtype=np.float64).reshape(tuple(shape)))
+    gu = np.empty_like(u0)
+    gc = np.empty_like(c)
+    loss = np.zeros(1, dtype=np.float64)
+    _check(_load().oracle_adjoint_vc_f64(d, r, pattern, _p(n, ctypes.c_int64), _p(c, ctypes.c_double), bkind,
+                                         float(bval), _p(u0, ctypes.c_double), _p(tg, ctypes.c_double), int(T),
+                                         _p(gu, ctypes.c_double), _p(gc, ctypes.c_double),
+                                         _p(loss, ctypes.c_double)), "adjoint_vc")
+    return float(loss[0]), gu, gc.reshape((-1,) + tuple(shape))
 
 
 def total(u) -> float:

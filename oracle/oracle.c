@@ -368,6 +368,130 @@ int oracle_adjoint_f64(int d, int r, int pattern, const int64_t *n, const double
     return 0;
 }
 
+/* ------------------------------------------- variable coefficients
+ * The same sweep with a coefficient per offset and per grid point (not in
+ * the paper; the variable-coefficient form of the Section 1 definition):
+ *     u_{t+1}[x] = sum_o c_o[x] * u_t(x + o),
+ * c stored offset-major in compact order: c[j * N + x] for the j-th compact
+ * offset.  Same boundary rule, same summation order. */
+
+static void step_vc_f64(const or_geom *g, const double *c, double bval, const double *src, double *dst)
+{
+    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2], N = n0 * n1 * n2;
+    int64_t rows = n0 * n1;
+#pragma omp parallel for schedule(static)
+    for (int64_t row = 0; row < rows; ++row) {
+        int64_t i0 = row / n1, i1 = row % n1;
+        for (int64_t i2 = 0; i2 < n2; ++i2) {
+            const int64_t x = (i0 * n1 + i1) * n2 + i2;
+            double acc = 0.0;
+            for (int j = 0; j < g->np; ++j) {
+                int64_t lin;
+                double v = resolve(g, i0 + g->off[j][0], i1 + g->off[j][1], i2 + g->off[j][2], &lin) ? src[lin] : bval;
+                acc = acc + c[(int64_t)g->cidx[j] * N + x] * v;
+            }
+            dst[x] = acc;
+        }
+    }
+}
+
+int oracle_run_vc_f64(int d, int r, int pattern, const int64_t *n, const double *c, int bkind, double bval,
+                      const double *u0, int64_t T, double *uT)
+{
+    or_geom g;
+    if (or_setup(&g, d, r, pattern, n, bkind) || !c || !u0 || !uT || T < 0) return -1;
+    int64_t N = g.n[0] * g.n[1] * g.n[2];
+    double *a = (double *)malloc(sizeof(double) * N), *b = (double *)malloc(sizeof(double) * N);
+    if (!a || !b) { free(a); free(b); return -2; }
+    memcpy(a, u0, sizeof(double) * N);
+    for (int64_t t = 0; t < T; ++t) { step_vc_f64(&g, c, bval, a, b); double *s = a; a = b; b = s; }
+    memcpy(uT, a, sizeof(double) * N);
+    free(a); free(b);
+    return 0;
+}
+
+static void step_vc_u32(const or_geom *g, const uint32_t *c, uint32_t bval, const uint32_t *src, uint32_t *dst)
+{
+    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2], N = n0 * n1 * n2;
+    int64_t rows = n0 * n1;
+#pragma omp parallel for schedule(static)
+    for (int64_t row = 0; row < rows; ++row) {
+        int64_t i0 = row / n1, i1 = row % n1;
+        for (int64_t i2 = 0; i2 < n2; ++i2) {
+            const int64_t x = (i0 * n1 + i1) * n2 + i2;
+            uint32_t acc = 0u;
+            for (int j = 0; j < g->np; ++j) {
+                int64_t lin;
+                uint32_t v = resolve(g, i0 + g->off[j][0], i1 + g->off[j][1], i2 + g->off[j][2], &lin) ? src[lin] : bval;
+                acc = acc + c[(int64_t)g->cidx[j] * N + x] * v;
+            }
+            dst[x] = acc;
+        }
+    }
+}
+
+int oracle_run_vc_u32(int d, int r, int pattern, const int64_t *n, const uint32_t *c, int bkind, uint32_t bval,
+                      const uint32_t *u0, int64_t T, uint32_t *uT)
+{
+    or_geom g;
+    if (or_setup(&g, d, r, pattern, n, bkind) || !c || !u0 || !uT || T < 0) return -1;
+    int64_t N = g.n[0] * g.n[1] * g.n[2];
+    uint32_t *a = (uint32_t *)malloc(sizeof(uint32_t) * N), *b = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    if (!a || !b) { free(a); free(b); return -2; }
+    memcpy(a, u0, sizeof(uint32_t) * N);
+    for (int64_t t = 0; t < T; ++t) { step_vc_u32(&g, c, bval, a, b); uint32_t *s = a; a = b; b = s; }
+    memcpy(uT, a, sizeof(uint32_t) * N);
+    free(a); free(b);
+    return 0;
+}
+
+/* loss = 0.5 * sum (u_T - target)^2 of the variable-coefficient sweep;
+ * returns the loss, d loss / d u0 and d loss / d c (same layout as c):
+ *     d loss / d c_o[x] = sum_t lam_{t+1}[x] * u_t(x + o)   (boundary values included)
+ *     lam_t[y] = sum over (x, o) with x + o resolving to y of c_o[x] lam_{t+1}[x]. */
+int oracle_adjoint_vc_f64(int d, int r, int pattern, const int64_t *n, const double *c, int bkind, double bval,
+                          const double *u0, const double *target, int64_t T,
+                          double *grad_u0, double *grad_c, double *loss)
+{
+    or_geom g;
+    if (or_setup(&g, d, r, pattern, n, bkind) || !c || !u0 || !target || !grad_u0 || !grad_c || !loss || T < 0)
+        return -1;
+    const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2], N = n0 * n1 * n2;
+    double *U = (double *)malloc(sizeof(double) * N * (T + 1));
+    double *lam = (double *)malloc(sizeof(double) * N), *tmp = (double *)malloc(sizeof(double) * N);
+    if (!U || !lam || !tmp) { free(U); free(lam); free(tmp); return -2; }
+    memcpy(U, u0, sizeof(double) * N);
+    for (int64_t t = 0; t < T; ++t) step_vc_f64(&g, c, bval, U + t * N, U + (t + 1) * N);
+    double L = 0.0;
+    for (int64_t i = 0; i < N; ++i) { double e = U[T * N + i] - target[i]; L = L + 0.5 * e * e; lam[i] = e; }
+    *loss = L;
+    for (int64_t i = 0; i < (int64_t)g.np * N; ++i) grad_c[i] = 0.0;
+    for (int64_t t = T - 1; t >= 0; --t) {
+        const double *Ut = U + t * N;
+        memset(tmp, 0, sizeof(double) * N);
+        for (int64_t i0 = 0; i0 < n0; ++i0)
+            for (int64_t i1 = 0; i1 < n1; ++i1)
+                for (int64_t i2 = 0; i2 < n2; ++i2) {
+                    const int64_t x = (i0 * n1 + i1) * n2 + i2;
+                    double l = lam[x];
+                    for (int j = 0; j < g.np; ++j) {
+                        int64_t lin;
+                        const int64_t cj = (int64_t)g.cidx[j] * N + x;
+                        if (resolve(&g, i0 + g.off[j][0], i1 + g.off[j][1], i2 + g.off[j][2], &lin)) {
+                            grad_c[cj] = grad_c[cj] + l * Ut[lin];
+                            tmp[lin] = tmp[lin] + c[cj] * l;
+                        } else {
+                            grad_c[cj] = grad_c[cj] + l * bval;
+                        }
+                    }
+                }
+        double *s = lam; lam = tmp; tmp = s;
+    }
+    memcpy(grad_u0, lam, sizeof(double) * N);
+    free(U); free(lam); free(tmp);
+    return 0;
+}
+
 /* ------------------------------------------------------------ reductions */
 
 int oracle_sum_f64(int64_t N, const double *u, double *out)
