@@ -38,6 +38,7 @@ METRIC = "GStencil/s and % HBM roofline, time-fused vs plain 1-step sweep at sta
 WORKLOADS = {
     "2d5p": (synth.c2_2d5p, "f32"),
     "2d9p": (synth.c2_2d9p, "f32"),
+    "2d5p_bf16": (synth.c2_2d5p, "bf16"),
     "2d5p_f64": (synth.c2_2d5p, "f64"),
     "2d9p_f64": (synth.c2_2d9p, "f64"),
     "3d7p": (synth.c3_3d7p, "f32"),
@@ -45,10 +46,11 @@ WORKLOADS = {
     "3d7p_bf16": (synth.c3_3d7p, "bf16"),
     "3d27p_bf16": (synth.c3_3d27p, "bf16"),
     "1d3p_f64": (synth.c1_1d3p, "f64"),
+    "1d3p_int": (synth.c1_1d3p_int, "i32"),
 }
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture, keyed by workload, k, tile height and a hash of the kernel sources
+# capture, keyed by workload, k, tile length and a hash of the kernel sources
 # it was measured on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 2D 5-point 8192^2 FP32, T = 64, k = 4, 64-row tiles: all 16 passes in one
@@ -56,15 +58,25 @@ NCU_TRAFFIC = {
     "2d5p:k4:rows64:a76529d36e34ef8c": 9290449000,
 }
 
-KERNEL_SOURCES = ["paper_2103_08825_gb300/csrc/k_fused2d.cuh", "paper_2103_08825_gb300/csrc/common.cuh"]
+CSRC = "paper_2103_08825_gb300/csrc/"
+KERNEL_SOURCES = {
+    1: [CSRC + "k_fused1d.cuh", CSRC + "k_fused2d.cuh", CSRC + "common.cuh"],
+    2: [CSRC + "k_fused2d.cuh", CSRC + "common.cuh"],
+    3: [CSRC + "k_fused3d.cuh", CSRC + "k_fused2d.cuh", CSRC + "common.cuh"],
+}
 
 
-def kernel_hash() -> str:
+def kernel_hash(d: int) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[d]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def fma_per_update(p) -> int:
+    """Algorithmic fused multiply-adds per point update (one per stencil term)."""
+    return synth.npoints(p.d, p.r, p.pattern)
 
 
 def measured_peaks():
@@ -177,10 +189,35 @@ def oracle_sample(p, budget_s: float):
     return upd / dt / 1e9, desc, dt
 
 
+def oracle_one_thread(workload: str, budget_s: float):
+    """The same oracle sample on one host thread (OpenMP limited to 1), in a
+    child process so that the parent's thread pool is untouched."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", workload, "--budget", str(budget_s)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=20 * budget_s + 120)
+        line = [x for x in out.stdout.splitlines() if x.startswith("{")][-1]
+        return json.loads(line)
+    except Exception as e:   # reported, not fatal: the baseline is context
+        return {"error": str(e)[:200]}
+
+
+def run_oracle_sample(args):
+    """--oracle-sample: print one JSON record of oracle_sample (used by
+    oracle_one_thread)."""
+    import oracle
+    maker, _ = WORKLOADS[args.oracle_sample]
+    rate, desc, secs = oracle_sample(maker(), args.budget)
+    print(json.dumps({"value": rate, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
+                      "sample": desc + f" ({secs:.1f} s)"}), flush=True)
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host cores, each step a bounded
-    sample of the workload."""
-    maker, _ = WORKLOADS[args.workload]
+    sample of the workload: the first rows of the grid advanced the full T
+    steps in one oracle call, so that the call's allocation and copies are
+    amortised over T sweeps as in the GPU run."""
+    maker, _ = WORKLOADS[args.workload] if args.workload in WORKLOADS else WORKLOADS["2d5p"]
     p = maker()
     if rank != 0:
         return
@@ -188,16 +225,15 @@ def run_reference(args, rank, world):
     oracle.build()
     total = args.steps + args.warmup
     per_step_budget = max(0.05, min(2.0, 150.0 / max(1, total)))
-    rate, desc, _ = oracle_sample(p, per_step_budget)
-    # fixed sample for all steps
-    sub = list(p.shape)
+    rate, _, _ = oracle_sample(p, per_step_budget)
     upd_target = rate * 1e9 * per_step_budget
     inner = float(np.prod(p.shape[1:])) if p.d > 1 else 1.0
-    steps = 1
+    sub = list(p.shape)
+    steps = p.T
     if p.d > 1:
-        sub[0] = int(max(1, min(p.shape[0], upd_target / inner)))
+        sub[0] = int(max(1, min(p.shape[0], upd_target / (inner * steps))))
     else:
-        sub[0] = int(max(64, min(p.shape[0], upd_target)))
+        sub[0] = int(max(64, min(p.shape[0], upd_target / steps)))
     u0 = synth.uniform01(p.seed, int(np.prod(sub))).reshape(sub)
     for _ in range(args.warmup):
         oracle.run(p.d, p.r, p.pattern, tuple(sub), p.weights, p.bkind, p.bval, u0, steps)
@@ -207,12 +243,14 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     upd = float(np.prod(sub)) * steps * args.steps
     value = upd / dt / 1e9
-    sample = f"FP64 oracle on the first {sub[0]} of {p.shape[0]} outer rows, {steps} step per bench step"
+    sample = (f"FP64 oracle on the first {sub[0]} of {p.shape[0]} outer rows, all {steps} steps in one call per "
+              f"bench step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GStencil/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded uniform[0,1))",
-            "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T},
+            "config": {"workload": workload_name(args.workload if args.workload in WORKLOADS else "2d5p", p),
+                       "grid": list(p.shape), "T": p.T},
             "cpu_baseline": {"value": value, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GStencil/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -256,6 +294,21 @@ def _events_ms(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def fourier_mode_decay(shape, kvec, weights, T):
+    """A periodic 2D Fourier mode cos(2 pi (ky y / ny + kx x / nx)) and its
+    image after T steps of a 3x3 correlation with `weights` (box order): the
+    mode times lam^T with lam = sum_o w_o exp(i theta . o), real part taken.
+    Closed form in FP64; no oracle involved."""
+    ny, nx = shape
+    ty, tx = 2 * np.pi * kvec[0] / ny, 2 * np.pi * kvec[1] / nx
+    lam = 0j
+    for j, (oy, ox) in enumerate(compact_offsets(2, 1, synth.BOX)):
+        lam += weights[j] * np.exp(1j * (ty * oy + tx * ox))
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ph = np.exp(1j * (ty * yy + tx * xx))
+    return ph.real, (lam ** T * ph).real
+
+
 def run_batch(args):
     """Batched workload: 256 periodic 2D 9-point FP32 grids of uneven size and
     step count in one graph-captured persistent launch, against one
@@ -269,7 +322,12 @@ def run_batch(args):
     b = sg.stencil_batch_create([p.shape for p in probs], [p.weights for p in probs], [p.T for p in probs],
                                 synth.BOX, 1, synth.PERIODIC, 0.0, sg.STENCIL_F32)
     upd = float(sum(p.npts * p.T for p in probs))
+    tuned_ms = sg.stencil_batch_tune(b, xs, ys)
+    k_b, rows_b = sg.stencil_batch_get_config(b)
+    clocks = ClockSampler(None)
+    clocks.start()
     ms = _events_ms(lambda: sg.stencil_batch_run(b, xs, ys), args.steps, args.warmup)
+    clk = clocks.stop()
     if sg.stencil_batch_get_device_status(b) != 0:
         raise RuntimeError("batch status word reports a timeout")
     plans = [sg.stencil_plan_create(2, 1, p.shape, synth.BOX, p.weights, synth.PERIODIC, 0.0, sg.STENCIL_F32)
@@ -281,57 +339,131 @@ def run_batch(args):
 
     ms_sep = _events_ms(separate, max(3, args.steps // 4), 2)
     launches_sep = sum(sg.stencil_plan_launch_count(pl, p.T) for pl, p in zip(plans, probs))
+    # error against FP64: every member starts from a Fourier mode whose image
+    # after its T steps is known in closed form
+    modes, exps = [], []
+    for g, p in enumerate(probs):
+        kv = (1 + g % 3, 1 + (g // 3) % 4)
+        m0, mt = fourier_mode_decay(p.shape, kv, synth.f32_weights(p.weights), p.T)
+        modes.append(torch.from_numpy(m0.astype(np.float32)).cuda())
+        exps.append(mt)
+    outs = [torch.empty_like(m) for m in modes]
+    sg.stencil_batch_run(b, modes, outs)
+    torch.cuda.synchronize()
+    # the FP32 input mode is the FP64 mode rounded: compare normwise with a
+    # bound of a few FP32 roundings per step
+    err = max(float(np.max(np.abs(o.double().cpu().numpy() - e))) / max(1e-3, float(np.max(np.abs(e))))
+              for o, e in zip(outs, exps))
     peak, peak_kind = measured_peaks()
-    passes = sum(-(-p.T // 4) * p.npts for p in probs)      # k = 4 passes per grid
+    passes = sum(-(-p.T // k_b) * p.npts for p in probs)
     achieved = 2.0 * 4 * passes / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        # a bounded sample: the first grids of the batch, each with its own T
+        t0 = time.perf_counter()
+        done_upd = 0.0
+        for p in probs:
+            u0 = synth.uniform01(p.seed, p.npts).reshape(p.shape)
+            oracle.run(2, 1, synth.BOX, p.shape, p.weights, synth.PERIODIC, 0.0, u0, p.T)
+            done_upd += p.npts * p.T
+            if time.perf_counter() - t0 > 15.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": done_upd / dt / 1e9, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"FP64 oracle over the first grids of the batch ({done_upd:.3g} updates, {dt:.1f} s)"}
     line = {"metric": "batched GStencil/s, one persistent graph-captured launch vs one stencil_run per grid",
             "value": upd / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic (256 seeded grids, sides log-uniform 64..2048, T uniform 8..128, periodic)",
             "config": {"workload": "batch 256 x 2d9p periodic F32", "grids": len(probs), "points": sum(p.npts for p in probs),
-                       "updates": upd, "k": 4},
+                       "updates": upd, "k": k_b, "tile_rows": rows_b, "tuned_ms": tuned_ms,
+                       "l2": "336 MB of grids, larger than L2; no flush"},
             "separate_runs": {"value": upd / (ms_sep * 1e-3) / 1e9, "ms_per_step": ms_sep, "launches": launches_sep},
             "speedup_vs_separate": ms_sep / ms,
+            "error": {"kind": "periodic Fourier mode per grid against lam^T * mode (FP64 closed form), max over "
+                              "grids of the normwise error", "value": err, "tolerance": 1e-5},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "bytes_per_step": 2.0 * 4 * passes},
+                         "traffic": None, "peak_kind": peak_kind, "bytes_per_step": 2.0 * 4 * passes},
+            "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": args.steps * sg.stencil_batch_launch_count(b)}
     print(json.dumps(line), flush=True)
 
 
 def run_adjoint(args):
     """Differentiation workload: 3D 7-point periodic 256^3 FP32, T = 64,
-    checkpoints every 8: backward (stencil_adjoint_run) against forward."""
+    checkpoints every 8: the forward sweep keeping its checkpoints
+    (stencil_run_checkpointed) and the backward sweep from them
+    (stencil_adjoint_from_checkpoints), timed apart."""
     import torch
     import paper_2103_08825_gb300 as sg
     sg.load()
     p = synth.c5_adjoint()
+    c = p.extra["ckpt_every"]
     u0 = torch.from_numpy(synth.uniform01(p.seed, p.npts).reshape(p.shape).astype(np.float32)).cuda()
     tg = torch.from_numpy(synth.uniform01(p.extra["target_seed"], p.npts).reshape(p.shape).astype(np.float32)).cuda()
     plan = sg.stencil_plan_create(3, 1, p.shape, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_F32)
     sg.stencil_plan_tune(plan, p.T)
     y = torch.empty_like(u0)
+    ck = torch.empty((sg.checkpoint_count(p.T, c),) + p.shape, dtype=torch.float32, device="cuda")
     gu = torch.empty_like(u0)
     gw = torch.empty(7, dtype=torch.float64, device="cuda")
-    ms_f = _events_ms(lambda: sg.stencil_run(plan, u0, y, p.T), args.steps, args.warmup)
+    clocks = ClockSampler(None)
+    clocks.start()
+    ms_plain_fwd = _events_ms(lambda: sg.stencil_run(plan, u0, y, p.T), args.steps, args.warmup)
+    ms_f = _events_ms(lambda: sg.stencil_run_checkpointed(plan, u0, y, p.T, c, ck), args.steps, args.warmup)
     g = (y - tg).contiguous()
-    ms_b = _events_ms(lambda: sg.stencil_adjoint_run(plan, u0, g, p.T, p.extra["ckpt_every"], gu, gw),
+    ms_b = _events_ms(lambda: sg.stencil_adjoint_from_checkpoints(plan, u0, ck, g, p.T, c, gu, gw),
                       max(3, args.steps // 4), 2)
+    clk = clocks.stop()
     upd = float(p.npts) * p.T
     peak, peak_kind = measured_peaks()
-    # backward bytes: checkpoint forward (fused) + recompute (one step each)
-    # + adjoint steps (read lam and u, write lam: 12 bytes per point)
-    c = p.extra["ckpt_every"]
-    bytes_adj = p.npts * p.T * 12.0
-    line = {"metric": "adjoint GStencil/s (backward, checkpointed) and backward/forward time",
+    # backward bytes: recompute (read + write one grid per inner step) + the
+    # transposed steps (read lam and u, write lam)
+    recompute = (p.T - p.T // c) * 2.0 * 4 * p.npts
+    adjoint_steps = p.T * 3.0 * 4 * p.npts
+    bytes_b = recompute + adjoint_steps
+    cpu, err = None, None
+    if not args.no_cpu_baseline:
+        # the FP64 oracle adjoint on a 64^3 sample of the workload (same
+        # recipe, T and checkpoints), and the GPU adjoint on the same sample
+        import oracle
+        oracle.build()
+        sh = (64, 64, 64)
+        n = int(np.prod(sh))
+        su0 = synth.uniform01(p.seed, n).reshape(sh).astype(np.float32)
+        stg = synth.uniform01(p.extra["target_seed"], n).reshape(sh).astype(np.float32)
+        t0 = time.perf_counter()
+        _, ogu, ogw = oracle.adjoint(3, 1, p.pattern, sh, synth.f32_weights(p.weights), p.bkind, p.bval,
+                                     su0.astype(np.float64), stg.astype(np.float64), p.T)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n * p.T / dt / 1e9, "unit": "GStencil/s (forward + backward)", "cores": oracle.threads(),
+               "kind": "oracle", "sample": f"FP64 oracle adjoint on a 64^3 periodic grid, T={p.T} ({dt:.1f} s)"}
+        sp = sg.stencil_plan_create(3, 1, sh, p.pattern, p.weights, p.bkind, p.bval, sg.STENCIL_F32)
+        x = torch.from_numpy(su0).cuda()
+        yy = torch.empty_like(x)
+        sk = sg.stencil_run_checkpointed(sp, x, yy, p.T, c)
+        sgu, sgw = sg.stencil_adjoint_from_checkpoints(sp, x, sk, (yy - torch.from_numpy(stg).cuda()).contiguous(),
+                                                       p.T, c)
+        torch.cuda.synchronize()
+        ew = float(np.max(np.abs(sgw.cpu().numpy() - ogw)) / np.max(np.abs(ogw)))
+        eu = float(np.max(np.abs(sgu.cpu().numpy().astype(np.float64) - ogu)) / np.max(np.abs(ogu)))
+        err = {"kind": "GPU adjoint against the FP64 oracle adjoint on the 64^3 sample", "grad_w_normwise": ew,
+               "grad_u0_normwise": eu, "tolerance": {"grad_w": 1e-5, "grad_u0": 1e-4}}
+    line = {"metric": "adjoint GStencil/s (backward from forward checkpoints) and backward/forward time",
             "value": upd / (ms_b * 1e-3) / 1e9, "unit": "GStencil/s", "n_gpus": 1, "dtype": "f32",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
             "data": "synthetic (seeded uniform[0,1) u0 and target)",
-            "config": {"workload": "3d7p 256^3 periodic F32 T=64 ckpt 8", "k_forward": sg.stencil_plan_get_k(plan)},
-            "forward": {"value": upd / (ms_f * 1e-3) / 1e9, "ms_per_step": ms_f},
+            "config": {"workload": "3d7p 256^3 periodic F32 T=64 ckpt 8", "k_forward": sg.stencil_plan_get_k(plan),
+                       "l2": "64 MiB grids, 9 checkpoints: working set larger than L2; no flush"},
+            "forward": {"value": upd / (ms_f * 1e-3) / 1e9, "ms_per_step": ms_f, "call": "stencil_run_checkpointed",
+                        "plain_forward_ms": ms_plain_fwd},
             "backward_over_forward": ms_b / ms_f,
-            "adjoint_step_bytes": bytes_adj, "ckpt_every": c,
-            "roofline_adjoint_steps_only": {"bound": "hbm", "bytes_per_step": bytes_adj, "peak": peak,
-                                            "peak_kind": peak_kind}}
+            "roofline": {"bound": "hbm", "achieved": bytes_b / (ms_b * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_b / (ms_b * 1e-3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_step": bytes_b},
+            "error": err, "cpu_baseline": cpu, "clocks": clk, "ckpt_every": c}
     print(json.dumps(line), flush=True)
 
 
@@ -346,8 +478,13 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0, help="2D tile height with --k (0 = the plan's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=0, help="steps for the plain sweep (0 = steps/4)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--budget", type=float, default=10.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.oracle_sample:
+        run_oracle_sample(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -375,7 +512,7 @@ def main():
 
     maker, dtn = WORKLOADS[args.workload]
     p = maker()
-    code = {"f32": sg.STENCIL_F32, "f64": sg.STENCIL_F64, "bf16": sg.STENCIL_BF16}[dtn]
+    code = {"f32": sg.STENCIL_F32, "f64": sg.STENCIL_F64, "bf16": sg.STENCIL_BF16, "i32": sg.STENCIL_I32}[dtn]
     tdt = sg.torch_dtype(code)
     esize = torch.tensor([], dtype=tdt).element_size()
     plan = sg.stencil_plan_create(p.d, p.r, p.shape, p.pattern, p.weights, p.bkind, p.bval, code)
@@ -383,6 +520,8 @@ def main():
 
     if p.d == 3 and p.bkind == synth.DIRICHLET:
         u0 = torch.from_numpy(synth.u0_modes_plus_noise(p, np.float32)).to(tdt)   # 8 sine modes + noise
+    elif dtn == "i32":
+        u0 = torch.from_numpy(synth.u0_int(p))
     else:
         u0 = torch.from_numpy(synth.uniform01(p.seed, p.npts).reshape(p.shape)).to(tdt)
     x = u0.to(dev)
@@ -403,10 +542,28 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # grids smaller than L2 (129 MB) are timed iteration by iteration, each
+    # after a write of a buffer twice the L2's size
+    flush_l2 = p.npts * esize < 256 * 2**20
+    flush_buf = torch.empty(64 * 2**20, dtype=torch.float32, device=dev) if flush_l2 else None
+
     def timed(fn, steps, warmup):
         for _ in range(warmup):
             fn()
         barrier()
+        if flush_l2:
+            total = 0.0
+            for _ in range(steps):
+                flush_buf.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+            barrier()
+            return max_over_ranks(total, dev, world)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -455,26 +612,79 @@ def main():
     if variant != sg.STENCIL_VARIANT_PLAIN:
         sg.stencil_plan_set_k(plan, k)
 
-    # roofline of the fused sweep: algorithmic bytes (one read and one write
-    # of every point per pass of k steps) over the timed step.  With the 2D
-    # persistent kernel one launch carries every pass of exactly k steps, so
-    # when T is a multiple of k the step is that single launch.
+    # Rooflines of the dominant launch, timed alone with CUDA events on the
+    # launching stream: with the persistent form that is the launch carrying
+    # the floor(T/k) passes of exactly k steps (a remainder of T mod k steps is
+    # a second, smaller launch); with one launch per pass (or step), one pass.
+    # HBM: algorithmic bytes = one read and one write of every point per pass.
+    # ALU: algorithmic FMAs = one per stencil term per update, against the
+    # measured FMA rate of the compute type (FP32 for FP32/BF16 storage, FP64).
     peak, peak_kind = measured_peaks()
     fused_now = variant != sg.STENCIL_VARIANT_PLAIN
-    passes = -(-p.T // k) if fused_now else p.T
+    kk = k if fused_now else 1
+    passes = -(-p.T // kk)
     bytes_step = 2.0 * p.npts * esize * passes
-    achieved = bytes_step / (ms_step * 1e-3) / 1e9
-    key = f"{args.workload}:k{k}:rows{sg.stencil_plan_get_tile_rows(plan)}:{kernel_hash()}"
+    if launches == 1:
+        t_dom, dom_passes = p.T, passes
+    elif launches == 2 and p.T // kk >= 2:
+        t_dom, dom_passes = kk * (p.T // kk), p.T // kk
+    else:
+        t_dom, dom_passes = kk, 1
+
+    def dom_step():
+        sg.stencil_run(plan, x, y, t_dom, stream)
+
+    dom_reps = max(3, int(args.steps * passes / max(1, dom_passes)) // 2)
+    ms_dom = timed(dom_step, dom_reps, 3) / dom_reps
+    dom_bytes = 2.0 * p.npts * esize * dom_passes
+    achieved = dom_bytes / (ms_dom * 1e-3) / 1e9
+    key = f"{args.workload}:k{k}:rows{sg.stencil_plan_get_tile_rows(plan)}:{kernel_hash(p.d)}"
     traffic = NCU_TRAFFIC.get(key)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+    hbm_roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": sg.stencil_plan_describe(plan),
-                "bytes_per_launch": bytes_step / launches, "bytes_per_pass": 2.0 * p.npts * esize,
-                "passes_per_step": passes, "launches_per_step": launches}
+                "bytes_per_launch": dom_bytes, "launch_ms": ms_dom, "bytes_per_pass": 2.0 * p.npts * esize,
+                "passes_per_launch": dom_passes, "passes_per_step": passes, "launches_per_step": launches}
+    alu_roof = None
+    if dtn != "i32":
+        ctype = sg.STENCIL_F64 if dtn == "f64" else sg.STENCIL_F32
+        fma_rate = sg.stencil_probe_fma_rate(ctype)
+        fma_dom = float(p.npts) * t_dom * fma_per_update(p)
+        alu_ach = 2.0 * fma_dom / (ms_dom * 1e-3) / 1e12
+        alu_peak = 2.0 * fma_rate / 1e12
+        alu_roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": alu_ach / alu_peak, "traffic": None,
+                    "peak_kind": f"measured ({'FP64' if dtn == 'f64' else 'FP32'} FMA probe, "
+                                 "stencil_probe_fma_rate)",
+                    "flops_per_launch": 2.0 * fma_dom, "launch_ms": ms_dom,
+                    "fma_per_update": fma_per_update(p)}
+    # the binding roof is the one the launch runs closer to
+    if alu_roof is not None and alu_roof["frac"] > hbm_roof["frac"]:
+        roofline, other_roof = alu_roof, hbm_roof
+    else:
+        roofline, other_roof = hbm_roof, alu_roof
 
     # error at the timed configuration: a Dirichlet sine mode must decay by
     # lam^T (closed form, no oracle involved)
     err = None
-    if p.bkind == synth.DIRICHLET and p.r == 1:
+    if dtn == "i32" and p.d == 1 and p.r == 1 and list(p.weights) == [2.0, 1.0, 1.0]:
+        # integer mode: from a unit impulse, T steps of the 1-2-1 stencil give
+        # the binomial row C(2T, T+m) (mod 2^32 in uint32), exactly
+        import math
+        c = p.shape[0] // 2
+        delta = torch.zeros(p.shape, dtype=tdt)
+        delta[c] = 1
+        xm = delta.to(dev)
+        ym = torch.empty_like(xm)
+        sg.stencil_run(plan, xm, ym, p.T, stream)
+        torch.cuda.synchronize()
+        got = ym.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+        exp = np.zeros(p.shape, dtype=np.int64)
+        for m in range(-p.T, p.T + 1):
+            exp[c + m] = math.comb(2 * p.T, p.T + m) % (1 << 32)
+        err = {"kind": "uint32 binomial closed form from a unit impulse, full grid",
+               "mismatches": int(np.count_nonzero(got != exp)), "tolerance": 0}
+        del xm, ym
+    elif p.bkind == synth.DIRICHLET and p.r == 1:
         ks = (3, 5, 7)[:p.d]
         vecs = [synth.sine_mode_1d(p.shape[a], ks[a]) for a in range(p.d)]
         phi = vecs[0]
@@ -517,7 +727,8 @@ def main():
         import oracle
         rate, desc, secs = oracle_sample(p, 20.0)
         cpu = {"value": rate, "unit": "GStencil/s", "cores": oracle.threads(), "kind": "oracle",
-               "sample": desc + f" ({secs:.1f} s)", "host_cores": host_cores()}
+               "sample": desc + f" ({secs:.1f} s)", "host_cores": host_cores(),
+               "one_thread": oracle_one_thread(args.workload, 10.0)}
 
     line = {"metric": METRIC, "value": value, "unit": "GStencil/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -526,14 +737,17 @@ def main():
                        "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan),
                                  "launch": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass"}[variant]}
                        if tuned else None,
-                       "l2": f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush",
+                       "l2": (f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush"
+                              if not flush_l2 else
+                              f"inputs smaller than L2 ({p.npts * esize / 2**20:.2f} MiB): L2 flushed (256 MiB "
+                              "write) before every timed iteration, outside its events"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "plain_sweep": {"value": plain_value, "unit": "GStencil/s", "ms_per_step": ms_plain,
                             "launches_per_step": p.T},
             "one_step_fused_k1": {"value": one_step_fused, "unit": "GStencil/s"} if one_step_fused else None,
             "speedup_vs_plain": value / world / plain_value,
             "speedup_vs_best_one_step": value / world / max(plain_value, one_step_fused or 0.0),
-            "error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "error": err, "roofline": roofline, "roofline_other": other_roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches * args.steps, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -74,11 +74,18 @@ typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_ki
  * wait on their neighbours' completion of the previous pass.
  * PLAIN: one step per launch, each thread reading its own neighbours -- the
  * one-step-per-launch sweep the fused path is measured against.
- * FUSED_PER_PASS: the fused kernels with one launch per pass. */
+ * FUSED_PER_PASS: the fused kernels with one launch per pass.
+ * TESSELLATE: the paper's tessellate tiling (Section 3.4): time tiles of h
+ * levels (h = the plan's k, default 8; any h with 2 h r no longer than a
+ * segment), each in d + 1 stages of concurrent shrinking / expanding tiles
+ * that together update every point once per level -- no redundant work, one
+ * launch per stage; segments of the plan's tile length (default 2048, 64, 32
+ * points in 1D, 2D, 3D).  Results are bit-identical to the other forms. */
 typedef enum {
     STENCIL_VARIANT_FUSED = 0,
     STENCIL_VARIANT_PLAIN = 1,
-    STENCIL_VARIANT_FUSED_PER_PASS = 2
+    STENCIL_VARIANT_FUSED_PER_PASS = 2,
+    STENCIL_VARIANT_TESSELLATE = 3
 } stencil_variant_t;
 
 /* Stencil coefficients: `count` values in compact order (see above). */
@@ -129,6 +136,13 @@ stencil_status_t stencil_plan_get_variant(stencil_plan_t plan, int32_t *variant)
 stencil_status_t stencil_plan_set_tile_rows(stencil_plan_t plan, int32_t rows);
 stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t plan, int32_t *rows);
 
+/* Warps per CTA of the 2D fused kernels (each warp streams its own jobs; the
+ * block size sets how many share an SM's scheduling slot and shared-memory
+ * carve-out): 1..8, 0 = the default of 4.  The 1D and 3D kernels have fixed
+ * block sizes (a 3D CTA's 16 warps make up its 64-row window). */
+stencil_status_t stencil_plan_set_block_warps(stencil_plan_t plan, int32_t warps);
+stencil_status_t stencil_plan_get_block_warps(stencil_plan_t plan, int32_t *warps);
+
 /* Autotune the fusion depth, the launch form and the tile length:
  * times stencil_run for the one-step kernel and, for every supported k, the
  * fused kernels with one launch per pass and the persistent multi-pass
@@ -171,6 +185,51 @@ stencil_status_t stencil_run(stencil_plan_t plan, const void *u_in, void *u_out,
  * asynchronous engine transfers; pageable memory works but is slower. */
 stencil_status_t stencil_run_host(stencil_plan_t plan, const void *h_in, void *h_out, int64_t T, void *stream);
 
+/* In-place sweep (2D plans): u := T steps applied to u, with one grid of
+ * memory instead of two -- the GPU form of the paper's in-place update
+ * (Section 3.3, last paragraph: with k = 2 the input and output of a pass sit
+ * at even time levels, so one array suffices).  Tiles advance k steps per pass
+ * as in stencil_run (k = the plan's k, at most 4 for r = 1, 2 for r = 2 and 1
+ * for r = 3; the update order and so the
+ * result are stencil_run's, bit for bit) and overwrite their own cells; the
+ * cells within r k rows or H >= r k columns of every tile's border, which
+ * neighbouring tiles read, are kept in two plan-owned ring buffers (the pass
+ * before's values and this pass's), about 2 (2 r k / Ly + 2 H / BW) of a
+ * grid.  One launch per pass plus one to fill the rings.  u is a device
+ * pointer of the plan's shape and dtype. */
+stencil_status_t stencil_run_inplace(stencil_plan_t plan, void *u, int64_t T, void *stream);
+/* Device bytes stencil_run_inplace uses beyond the grid itself (the two ring
+ * buffers), for the plan's current k; stencil_run uses one grid. */
+stencil_status_t stencil_inplace_workspace_bytes(stencil_plan_t plan, int64_t *bytes);
+
+/* Variable-coefficient sweep: u_out := T steps of
+ *     u_{t+1}[x] = sum_o c_o[x] * u_t(x + o)
+ * with a coefficient per offset and per grid point (the Section 1 sweep with
+ * its weights made fields; not in the paper).  The plan gives the geometry,
+ * pattern, radius, boundary and dtype (F32, F64 or I32); its weights are not
+ * used.  `coef` is a device array of np x N values of the arithmetic type
+ * (float for F32, double for F64, int32 for I32), offset-major in compact
+ * order: coef[j * N + x] multiplies the j-th compact offset at point x.
+ * Terms are summed in the same order as stencil_run, so a constant field
+ * reproduces it bit for bit.  2D plans fuse k steps per pass (the plan's k,
+ * at most 4 for r = 1 and 2 for r = 2: the coefficient planes are read once
+ * per pass, (2 + np) s bytes per point and pass); r = 3 and 1D/3D plans run
+ * one step per launch.  u_out must not overlap u_in; a plan-owned grid holds
+ * the intermediate passes. */
+stencil_status_t stencil_run_vc(stencil_plan_t plan, const void *coef, const void *u_in, void *u_out, int64_t T,
+                                void *stream);
+
+/* Many host grids in a row, pipelined: h_out[i] := T steps applied to
+ * h_in[i] for i < n (host buffers of the plan's shape and dtype, each read or
+ * written during the call).  Two input and two output grids are kept on the
+ * device so that the host-to-device copy of grid i + 1 and the
+ * device-to-host copy of grid i - 1 run on two copy streams while grid i is
+ * swept on `stream`: with pinned buffers the time per grid approaches the
+ * longest of the three instead of their sum.  Synchronises `stream` before
+ * returning. */
+stencil_status_t stencil_run_host_many(stencil_plan_t plan, int64_t n, const void *const *h_in, void *const *h_out,
+                                       int64_t T, void *stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* The paper has no batched form: its experiments advance one grid at a time
@@ -199,6 +258,18 @@ stencil_status_t stencil_batch_destroy(stencil_batch_t batch);
 stencil_status_t stencil_batch_run(stencil_batch_t batch, const void *const *u_in, void *const *u_out,
                                    void *stream);
 stencil_status_t stencil_batch_get_device_status(stencil_batch_t batch);
+/* The batch's fusion depth k (1..4 for r = 1, 1..2 for r = 2; 0 = the
+ * largest) and tile height in rows (at least 4 r k; 0 = 64): every member's
+ * passes advance k steps (the first the remainder of T), in tiles of one
+ * 120-column band x tile_rows rows.  Changing them rebuilds the schedule and
+ * recaptures the graph on the next run. */
+stencil_status_t stencil_batch_set_config(stencil_batch_t batch, int32_t k, int32_t tile_rows);
+stencil_status_t stencil_batch_get_config(stencil_batch_t batch, int32_t *k, int32_t *tile_rows);
+/* Autotune k and the tile height on the caller's buffers (the batch is run
+ * several times per candidate, timed with CUDA events on `stream`) and keep
+ * the fastest; best_ms (may be NULL) receives its time. */
+stencil_status_t stencil_batch_tune(stencil_batch_t batch, const void *const *u_in, void *const *u_out, void *stream,
+                                    double *best_ms);
 /* Kernel launches per stencil_batch_run (the graph's kernel nodes). */
 stencil_status_t stencil_batch_launch_count(stencil_batch_t batch, int64_t *launches);
 
@@ -214,11 +285,30 @@ stencil_status_t stencil_batch_launch_count(stencil_batch_t batch, int64_t *laun
  * plan shape) and grad_w[j] = dL/dw_j (device, `count` doubles, compact
  * order).  The transposed sweep runs backward in time; forward states are
  * recomputed from checkpoints stored every `ckpt_every` steps (1 <= ckpt_every
- * <= T; the plan keeps ceil(T/ckpt_every) + ckpt_every grids of workspace).
+ * <= T): this call first runs stencil_run_checkpointed into plan-owned
+ * checkpoints, then stencil_adjoint_from_checkpoints (the plan keeps
+ * ceil(T/ckpt_every) + ckpt_every + 1 grids of workspace).
  * With a Dirichlet boundary the weight gradient includes the boundary value's
  * contributions. */
 stencil_status_t stencil_adjoint_run(stencil_plan_t plan, const void *u0, const void *grad_uT, int64_t T,
                                      int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream);
+
+/* The forward sweep of an F32 plan with checkpoints kept for the adjoint:
+ * u_T := T steps of u0 (as stencil_run, in segments of ckpt_every steps) and
+ * ckpts[m] := the state after (m + 1) ckpt_every steps for
+ * m = 0 .. ceil(T / ckpt_every) - 2 (caller-owned device buffer of that many
+ * grids; may be NULL when T <= ckpt_every).  The checkpoints cost no extra
+ * sweep: each segment writes its result there directly. */
+stencil_status_t stencil_run_checkpointed(stencil_plan_t plan, const void *u0, void *u_T, int64_t T,
+                                          int32_t ckpt_every, void *ckpts, void *stream);
+/* The backward sweep of stencil_adjoint_run from checkpoints that
+ * stencil_run_checkpointed took (same u0, T and ckpt_every): grad_u0 and
+ * grad_w as there, without re-running the forward sweep.  The weight gradient
+ * sums each thread's products of one step in FP32 and everything above that
+ * (warps, blocks, steps) in FP64. */
+stencil_status_t stencil_adjoint_from_checkpoints(stencil_plan_t plan, const void *u0, const void *ckpts,
+                                                  const void *grad_uT, int64_t T, int32_t ckpt_every, void *grad_u0,
+                                                  double *grad_w, void *stream);
 
 /* -------------------------------------------------------------- reductions */
 
@@ -260,6 +350,28 @@ stencil_status_t stencil_reduce(int32_t dtype, int64_t n, const void *u, const v
  * The paper has no counterpart to this entry point. */
 stencil_status_t stencil_reduce_noalloc(int32_t dtype, int64_t n, const void *u, const void *target, int32_t op,
                                         double *out, void *stream);
+
+/* -------------------------------------------------------------- diagnostics */
+
+/* Measured fused multiply-add throughput of the current device for `dtype`
+ * (F32 or F64), in FMAs per second: independent FMA chains on every SM, timed
+ * with CUDA events on `stream` (synchronises it).  Not in the paper: it gives
+ * the compute roof against which the sweeps that are bound by the FP32 pipe
+ * (the 3D 27-point box) or the FP64 pipe (every FP64 sweep on this GPU) are
+ * graded, the way a copy kernel gives the HBM roof. */
+stencil_status_t stencil_probe_fma_rate(int32_t dtype, double *fma_per_s, void *stream);
+
+/* Host-only (no device needed): the level counts of the tessellate tiling
+ * that STENCIL_VARIANT_TESSELLATE uses for a grid of `shape` (dim extents),
+ * radius, `levels` per time tile, segment length `tile` and periodic (1) or
+ * Dirichlet (0) boundary.  counts[(dim + 1) x N] receives, for each stage s
+ * and point x, the number of levels at which stage s updates x: in 1D stage 0
+ * gives each segment the paper's (0, 1, .., h, .., 1, 0) profile, stage 1 the
+ * complement, and the stages sum to `levels` at every point (Section 3.4,
+ * Fig. 6).  STENCIL_ERR_INVALID_ARG when a segment is shorter than
+ * 2 levels radius or the grid has more than 2^26 points. */
+stencil_status_t stencil_tess_counts(int32_t dim, const int64_t *shape, int32_t radius, int32_t levels, int32_t tile,
+                                     int32_t periodic, int32_t *counts);
 
 /* ------------------------------------------------------------------ status */
 

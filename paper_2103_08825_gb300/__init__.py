@@ -22,19 +22,22 @@ STENCIL_ERR_CUDA, STENCIL_ERR_TIMEOUT, STENCIL_ERR_INTERNAL = 4, 5, 6
 STENCIL_F64, STENCIL_F32, STENCIL_BF16, STENCIL_F16, STENCIL_I32 = 0, 1, 2, 3, 4
 STENCIL_STAR, STENCIL_BOX = 0, 1
 STENCIL_DIRICHLET, STENCIL_PERIODIC = 0, 1
-STENCIL_VARIANT_FUSED, STENCIL_VARIANT_PLAIN, STENCIL_VARIANT_FUSED_PER_PASS = 0, 1, 2
+STENCIL_VARIANT_FUSED, STENCIL_VARIANT_PLAIN, STENCIL_VARIANT_FUSED_PER_PASS, STENCIL_VARIANT_TESSELLATE = 0, 1, 2, 3
 STENCIL_REDUCE_SUM, STENCIL_REDUCE_SUMSQ, STENCIL_REDUCE_HALF_SQDIST = 0, 1, 2
 
 # Every symbol include/stencil.h declares (checked by the CPU test suite).
 EXPORTS = [
     "stencil_plan_create", "stencil_plan_destroy", "stencil_plan_set_k", "stencil_plan_get_k",
     "stencil_plan_max_k", "stencil_plan_set_variant", "stencil_plan_get_variant", "stencil_plan_set_tile_rows",
-    "stencil_plan_get_tile_rows",
+    "stencil_plan_get_tile_rows", "stencil_plan_set_block_warps", "stencil_plan_get_block_warps",
     "stencil_plan_tune", "stencil_plan_launch_count",
-    "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_batch_create",
-    "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status",
-    "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_reduce", "stencil_reduce_noalloc",
-    "stencil_get_device_status",
+    "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_run_host_many", "stencil_run_inplace",
+    "stencil_inplace_workspace_bytes", "stencil_run_vc", "stencil_batch_create",
+    "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status", "stencil_batch_set_config",
+    "stencil_batch_get_config", "stencil_batch_tune",
+    "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_run_checkpointed",
+    "stencil_adjoint_from_checkpoints", "stencil_reduce", "stencil_reduce_noalloc",
+    "stencil_get_device_status", "stencil_probe_fma_rate", "stencil_tess_counts",
     "stencil_status_string", "stencil_last_error",
 ]
 
@@ -78,22 +81,35 @@ def load(path: str | None = None):
         "stencil_plan_get_variant": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_set_tile_rows": (st, [vp, i32]),
         "stencil_plan_get_tile_rows": (st, [vp, ctypes.POINTER(i32)]),
+        "stencil_plan_set_block_warps": (st, [vp, i32]),
+        "stencil_plan_get_block_warps": (st, [vp, ctypes.POINTER(i32)]),
         "stencil_plan_tune": (st, [vp, i64, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
         "stencil_plan_launch_count": (st, [vp, i64, ctypes.POINTER(i64)]),
         "stencil_plan_describe": (st, [vp, ctypes.c_char_p, i32]),
         "stencil_run": (st, [vp, vp, vp, i64, vp]),
         "stencil_run_host": (st, [vp, vp, vp, i64, vp]),
+        "stencil_run_inplace": (st, [vp, vp, i64, vp]),
+        "stencil_run_host_many": (st, [vp, i64, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, vp]),
+        "stencil_inplace_workspace_bytes": (st, [vp, ctypes.POINTER(i64)]),
+        "stencil_run_vc": (st, [vp, vp, vp, vp, i64, vp]),
         "stencil_batch_create": (st, [ctypes.POINTER(vp), i32, i32, i32, ctypes.POINTER(i64),
                                       ctypes.POINTER(stencil_weights_t), ctypes.POINTER(i64),
                                       ctypes.POINTER(stencil_boundary_t), i32]),
         "stencil_batch_destroy": (st, [vp]),
         "stencil_batch_run": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
         "stencil_batch_get_device_status": (st, [vp]),
+        "stencil_batch_set_config": (st, [vp, i32, i32]),
+        "stencil_batch_get_config": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "stencil_batch_tune": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.POINTER(dbl)]),
         "stencil_batch_launch_count": (st, [vp, ctypes.POINTER(i64)]),
         "stencil_adjoint_run": (st, [vp, vp, vp, i64, i32, vp, vp, vp]),
+        "stencil_run_checkpointed": (st, [vp, vp, vp, i64, i32, vp, vp]),
+        "stencil_adjoint_from_checkpoints": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
         "stencil_reduce": (st, [i32, i64, vp, vp, i32, vp, vp]),
         "stencil_reduce_noalloc": (st, [i32, i64, vp, vp, i32, vp, vp]),
         "stencil_get_device_status": (st, [vp]),
+        "stencil_probe_fma_rate": (st, [i32, ctypes.POINTER(dbl), vp]),
+        "stencil_tess_counts": (st, [i32, ctypes.POINTER(i64), i32, i32, i32, i32, ctypes.POINTER(i32)]),
         "stencil_status_string": (ctypes.c_char_p, [st]),
         "stencil_batch_test_skip_publish": (st, [vp, i64]),
         "stencil_plan_test_poison_counter": (st, [vp, i64]),
@@ -205,6 +221,16 @@ def stencil_plan_get_tile_rows(plan: Plan) -> int:
     return r.value
 
 
+def stencil_plan_set_block_warps(plan: Plan, warps: int):
+    _check(load().stencil_plan_set_block_warps(plan.handle, int(warps)), "stencil_plan_set_block_warps")
+
+
+def stencil_plan_get_block_warps(plan: Plan) -> int:
+    r = ctypes.c_int32()
+    _check(load().stencil_plan_get_block_warps(plan.handle, ctypes.byref(r)), "stencil_plan_get_block_warps")
+    return r.value
+
+
 def stencil_plan_tune(plan: Plan, T: int, stream=None):
     k = ctypes.c_int32()
     ms = ctypes.c_double()
@@ -241,6 +267,39 @@ def stencil_run(plan: Plan, u_in, u_out, T: int, stream=None):
     return u_out
 
 
+def stencil_run_inplace(plan: Plan, u, T: int, stream=None):
+    """u := T steps applied to u, in place (2D plans; one grid of memory plus
+    two small ring buffers)."""
+    _check_grid(plan, u, "u")
+    _check(load().stencil_run_inplace(plan.handle, ctypes.c_void_p(u.data_ptr()), int(T), _stream_handle(stream)),
+           "stencil_run_inplace")
+    return u
+
+
+def stencil_inplace_workspace_bytes(plan: Plan) -> int:
+    n = ctypes.c_int64()
+    _check(load().stencil_inplace_workspace_bytes(plan.handle, ctypes.byref(n)), "stencil_inplace_workspace_bytes")
+    return n.value
+
+
+def stencil_run_vc(plan: Plan, coef, u_in, u_out, T: int, stream=None):
+    """u_out := T steps of the variable-coefficient sweep; coef is a CUDA
+    tensor of shape (npoints, *plan.shape) in the arithmetic type (float32 for
+    F32 plans, float64 for F64, int32 for I32), compact offset order."""
+    import torch
+    _check_grid(plan, u_in, "u_in")
+    _check_grid(plan, u_out, "u_out")
+    ctype = {STENCIL_F32: torch.float32, STENCIL_F64: torch.float64, STENCIL_I32: torch.int32}.get(plan.dtype)
+    if ctype is None:
+        raise ValueError("variable coefficients support F32, F64 and I32 plans")
+    if (not coef.is_cuda or not coef.is_contiguous() or coef.dtype != ctype or coef.device != u_in.device
+            or tuple(coef.shape) != (len(plan.weights),) + plan.shape):
+        raise ValueError(f"coef must be a contiguous {ctype} CUDA tensor of shape {(len(plan.weights),) + plan.shape}")
+    _check(load().stencil_run_vc(plan.handle, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(u_in.data_ptr()),
+                                 ctypes.c_void_p(u_out.data_ptr()), int(T), _stream_handle(stream)), "stencil_run_vc")
+    return u_out
+
+
 def stencil_run_host(plan: Plan, h_in, h_out, T: int, stream=None):
     """Host-buffer run (numpy arrays or CPU tensors); synchronises."""
     def ptr(a):
@@ -248,6 +307,21 @@ def stencil_run_host(plan: Plan, h_in, h_out, T: int, stream=None):
     _check(load().stencil_run_host(plan.handle, ctypes.c_void_p(ptr(h_in)), ctypes.c_void_p(ptr(h_out)), int(T),
                                    _stream_handle(stream)), "stencil_run_host")
     return h_out
+
+
+def stencil_run_host_many(plan: Plan, h_ins, h_outs, T: int, stream=None):
+    """h_outs[i] := T steps of h_ins[i] (host arrays or CPU tensors; pinned
+    memory makes the copies overlap the sweeps); synchronises."""
+    def ptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    n = len(h_ins)
+    if len(h_outs) != n:
+        raise ValueError("one output per input")
+    pin = (ctypes.c_void_p * max(n, 1))(*[ptr(a) for a in h_ins])
+    pout = (ctypes.c_void_p * max(n, 1))(*[ptr(a) for a in h_outs])
+    _check(load().stencil_run_host_many(plan.handle, n, pin, pout, int(T), _stream_handle(stream)),
+           "stencil_run_host_many")
+    return h_outs
 
 
 def stencil_get_device_status(plan: Plan) -> int:
@@ -300,6 +374,26 @@ def stencil_reduce_noalloc(u, op: int, target=None, out=None, stream=None):
         _check(load().stencil_reduce_noalloc(_dtype_code(u.dtype), u.numel(), ctypes.c_void_p(u.data_ptr()), tp,
                                              int(op), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
                "stencil_reduce_noalloc")
+    return out
+
+
+def stencil_probe_fma_rate(dtype: int, stream=None) -> float:
+    """Measured FMAs per second of the current GPU in F32 or F64."""
+    r = ctypes.c_double()
+    _check(load().stencil_probe_fma_rate(int(dtype), ctypes.byref(r), _stream_handle(stream)),
+           "stencil_probe_fma_rate")
+    return r.value
+
+
+def stencil_tess_counts(shape, radius: int, levels: int, tile: int, periodic: bool):
+    """Host-only: (d + 1, *shape) int32 array, the levels at which each stage of
+    one tessellation time tile updates each point."""
+    import numpy as np
+    d = len(shape)
+    n = (ctypes.c_int64 * d)(*[int(v) for v in shape])
+    out = np.zeros((d + 1,) + tuple(int(v) for v in shape), dtype=np.int32)
+    _check(load().stencil_tess_counts(d, n, int(radius), int(levels), int(tile), 1 if periodic else 0,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "stencil_tess_counts")
     return out
 
 
@@ -357,6 +451,27 @@ def stencil_batch_run(batch: Batch, u_in, u_out, stream=None):
     return u_out
 
 
+def stencil_batch_set_config(batch: Batch, k: int, tile_rows: int):
+    _check(load().stencil_batch_set_config(batch.handle, int(k), int(tile_rows)), "stencil_batch_set_config")
+
+
+def stencil_batch_get_config(batch: Batch):
+    k, rows = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().stencil_batch_get_config(batch.handle, ctypes.byref(k), ctypes.byref(rows)), "stencil_batch_get_config")
+    return k.value, rows.value
+
+
+def stencil_batch_tune(batch: Batch, u_in, u_out, stream=None) -> float:
+    """Choose the batch's k and tile height by timing runs on these tensors."""
+    n = len(batch.shapes)
+    pin = (ctypes.c_void_p * n)(*[t.data_ptr() for t in u_in])
+    pout = (ctypes.c_void_p * n)(*[t.data_ptr() for t in u_out])
+    ms = ctypes.c_double()
+    _check(load().stencil_batch_tune(batch.handle, pin, pout, _stream_handle(stream), ctypes.byref(ms)),
+           "stencil_batch_tune")
+    return ms.value
+
+
 def stencil_batch_get_device_status(batch: Batch) -> int:
     return int(load().stencil_batch_get_device_status(batch.handle))
 
@@ -384,28 +499,79 @@ def stencil_adjoint_run(plan: Plan, u0, grad_uT, T: int, ckpt_every: int, grad_u
     return grad_u0, grad_w
 
 
+def checkpoint_count(T: int, ckpt_every: int) -> int:
+    """Grids stencil_run_checkpointed stores for T steps."""
+    return max(0, -(-int(T) // int(ckpt_every)) - 1)
+
+
+def stencil_run_checkpointed(plan: Plan, u0, u_T, T: int, ckpt_every: int, ckpts=None, stream=None):
+    """u_T := T steps of u0, keeping the state every ckpt_every steps in
+    `ckpts` (a CUDA tensor of checkpoint_count(T, ckpt_every) grids, allocated
+    when None); returns ckpts."""
+    import torch
+    _check_grid(plan, u0, "u0")
+    _check_grid(plan, u_T, "u_T")
+    n = checkpoint_count(T, ckpt_every)
+    if ckpts is None:
+        ckpts = torch.empty((max(n, 1),) + plan.shape, dtype=u0.dtype, device=u0.device)
+    if (not ckpts.is_cuda or not ckpts.is_contiguous() or ckpts.dtype != u0.dtype
+            or ckpts.numel() < n * u0.numel()):
+        raise ValueError(f"ckpts must be a contiguous CUDA tensor of at least {n} grids")
+    _check(load().stencil_run_checkpointed(plan.handle, ctypes.c_void_p(u0.data_ptr()), ctypes.c_void_p(u_T.data_ptr()),
+                                           int(T), int(ckpt_every), ctypes.c_void_p(ckpts.data_ptr()),
+                                           _stream_handle(stream)), "stencil_run_checkpointed")
+    return ckpts
+
+
+def stencil_adjoint_from_checkpoints(plan: Plan, u0, ckpts, grad_uT, T: int, ckpt_every: int, grad_u0=None,
+                                     grad_w=None, stream=None):
+    """The backward sweep from stencil_run_checkpointed's checkpoints."""
+    import torch
+    _check_grid(plan, u0, "u0")
+    _check_grid(plan, grad_uT, "grad_uT")
+    if ckpts.numel() < checkpoint_count(T, ckpt_every) * u0.numel() or not ckpts.is_contiguous():
+        raise ValueError("ckpts holds fewer grids than T / ckpt_every needs")
+    if grad_u0 is None:
+        grad_u0 = torch.empty_like(u0)
+    if grad_w is None:
+        grad_w = torch.empty(len(plan.weights), dtype=torch.float64, device=u0.device)
+    _check_grid(plan, grad_u0, "grad_u0")
+    _check(load().stencil_adjoint_from_checkpoints(
+        plan.handle, ctypes.c_void_p(u0.data_ptr()), ctypes.c_void_p(ckpts.data_ptr()),
+        ctypes.c_void_p(grad_uT.data_ptr()), int(T), int(ckpt_every), ctypes.c_void_p(grad_u0.data_ptr()),
+        ctypes.c_void_p(grad_w.data_ptr()), _stream_handle(stream)), "stencil_adjoint_from_checkpoints")
+    return grad_u0, grad_w
+
+
 def _autograd_fn():
     import torch
 
     class StencilFn(torch.autograd.Function):
-        """u_T = T stencil steps of u0 with the plan's weights.  Backward runs
-        stencil_adjoint_run: gradients w.r.t. u0 and the weights (compact
-        order; `weights` must hold the plan's coefficients)."""
+        """u_T = T stencil steps of u0 with the plan's weights.  The forward
+        keeps a checkpoint every `ckpt_every` steps; backward runs the
+        transposed sweep from them and returns the gradients w.r.t. u0 and
+        the weights (compact order).  `weights` must hold the plan's
+        coefficients (checked)."""
 
         @staticmethod
         def forward(ctx, u0, weights, plan, T, ckpt_every=8):
+            w = weights.detach().double().cpu().tolist()
+            if len(w) != len(plan.weights) or any(a != float(b) for a, b in zip(w, plan.weights)):
+                raise ValueError("stencil_apply: `weights` differs from the plan's coefficients; create the plan "
+                                 "from these weights")
             u0 = u0.contiguous()
             out = torch.empty_like(u0)
-            stencil_run(plan, u0, out, T)
-            ctx.save_for_backward(u0)
-            ctx.plan, ctx.T, ctx.ckpt = plan, int(T), int(min(max(1, ckpt_every), max(1, T)))
+            c = int(min(max(1, ckpt_every), max(1, T)))
+            ckpts = stencil_run_checkpointed(plan, u0, out, T, c)
+            ctx.save_for_backward(u0, ckpts)
+            ctx.plan, ctx.T, ctx.ckpt = plan, int(T), c
             ctx.wdtype = weights.dtype
             return out
 
         @staticmethod
         def backward(ctx, grad_out):
-            (u0,) = ctx.saved_tensors
-            gu, gw = stencil_adjoint_run(ctx.plan, u0, grad_out.contiguous(), ctx.T, ctx.ckpt)
+            u0, ckpts = ctx.saved_tensors
+            gu, gw = stencil_adjoint_from_checkpoints(ctx.plan, u0, ckpts, grad_out.contiguous(), ctx.T, ctx.ckpt)
             return gu, gw.to(ctx.wdtype), None, None, None
 
     return StencilFn

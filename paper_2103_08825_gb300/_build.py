@@ -30,6 +30,27 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the GB300 stencil library needs the CUDA toolkit to build")
 
 
+_INCLUDE_RE = None
+
+
+def _local_deps(path: str, seen=None) -> set:
+    """The quoted #include files a source pulls in, transitively (the headers
+    of csrc/ and include/ it depends on)."""
+    global _INCLUDE_RE
+    import re
+    if _INCLUDE_RE is None:
+        _INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+    seen = set() if seen is None else seen
+    with open(path) as f:
+        text = f.read()
+    for name in _INCLUDE_RE.findall(text):
+        dep = os.path.normpath(os.path.join(os.path.dirname(path), name))
+        if os.path.exists(dep) and dep not in seen:
+            seen.add(dep)
+            _local_deps(dep, seen)
+    return seen
+
+
 def _stale(obj: str, src: str, deps) -> bool:
     if not os.path.exists(obj):
         return True
@@ -41,14 +62,12 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     nvcc = _nvcc()
     os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    deps = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
-                  glob.glob(os.path.join(INCLUDE, "*.h")))
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
                     "-I", INCLUDE, "--expt-relaxed-constexpr"]
 
     def one(src):
         obj = os.path.join(OUT, "obj", os.path.basename(src)[:-3] + ".o")
-        if not force and not _stale(obj, src, deps):
+        if not force and not _stale(obj, src, _local_deps(src)):
             return obj, ""
         tmp = obj + f".tmp{os.getpid()}"
         cmd = [nvcc, *flags, "-c", src, "-o", tmp]
@@ -58,6 +77,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         os.replace(tmp, obj)
         return obj, p.stderr
 
+    # compile the longest translation units first (they set the build's length)
+    srcs.sort(key=lambda f: -os.path.getsize(f) - sum(os.path.getsize(d) for d in _local_deps(f)))
     n = jobs or max(1, min(len(srcs), os.cpu_count() or 4))
     logs = []
     with cf.ThreadPoolExecutor(max_workers=n) as ex:

@@ -5,12 +5,15 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "plan.h"
 
@@ -109,13 +112,13 @@ static void compact_offsets(int d, int r, int pattern, int (*off)[3]) {
     }
 }
 
-static stencil_status_t cuda_fail(cudaError_t e, const char *what) {
+stencil_status_t cuda_fail(cudaError_t e, const char *what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return STENCIL_ERR_CUDA;
 }
 
 // 32 bytes: the status word at offset 0, the per-pass kernels' job tickets at 16
-static stencil_status_t ensure_status_word(stencil_plan_s *P) {
+stencil_status_t ensure_status_word(stencil_plan_s *P) {
     if (P->d_status) return STENCIL_OK;
     cudaError_t e = cudaMalloc(&P->d_status, 32);
     if (e != cudaSuccess) { P->d_status = nullptr; set_error("status word allocation failed"); return STENCIL_ERR_OOM; }
@@ -144,7 +147,7 @@ cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t
     return cudaSuccess;
 }
 
-static stencil_status_t ensure_buf(void **buf, size_t bytes) {
+stencil_status_t ensure_buf(void **buf, size_t bytes) {
     if (*buf) return STENCIL_OK;
     cudaError_t e = cudaMalloc(buf, bytes > 0 ? bytes : 16);
     if (e != cudaSuccess) {
@@ -269,6 +272,16 @@ stencil_status_t stencil_plan_create(stencil_plan_t *out, int32_t dim, int32_t r
         delete P;
         return cuda_fail(e, "no CUDA device");
     }
+    // experiment overrides: STENCIL_K (fusion depth) and STENCIL_TILE (tile
+    // length), applied where the kernels accept them
+    if (const char *ek = getenv("STENCIL_K")) {
+        const int k = atoi(ek);
+        if (k >= 1 && k <= std::max(fused_max_k(*P), 1)) P->k = k;
+    }
+    if (const char *et = getenv("STENCIL_TILE")) {
+        const int t = atoi(et);
+        if (t >= 0) P->tile_rows = t;
+    }
     *out = P;
     return STENCIL_OK;
 }
@@ -286,6 +299,13 @@ stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
     cudaFree(P->adj_ws);
     cudaFree(P->adj_partials);
     cudaFree(P->d_mp);
+    cudaFree(P->inpl_ws);
+    cudaFree(P->ckpt_ws);
+    for (int i = 0; i < 4; ++i) cudaFree(P->hm_buf[i]);
+    if (P->hm_ready) {
+        for (int i = 0; i < 2; ++i) cudaStreamDestroy(P->hm_st[i]);
+        for (int i = 0; i < 7; ++i) cudaEventDestroy(P->hm_ev[i]);
+    }
     cudaSetDevice(cur);
     delete P;
     return STENCIL_OK;
@@ -305,7 +325,8 @@ stencil_status_t stencil_plan_set_k(stencil_plan_t P, int32_t k) {
 
 stencil_status_t stencil_plan_get_k(stencil_plan_t P, int32_t *k) {
     if (!P || !k) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
-    *k = uses_fused(P) ? effective_k(P) : 1;
+    if (P->variant == STENCIL_VARIANT_TESSELLATE && !P->tuned_plain) *k = P->k > 0 ? P->k : 8;   // levels per time tile
+    else *k = uses_fused(P) ? effective_k(P) : 1;
     return STENCIL_OK;
 }
 
@@ -317,7 +338,7 @@ stencil_status_t stencil_plan_max_k(stencil_plan_t P, int32_t *kmax) {
 
 stencil_status_t stencil_plan_set_variant(stencil_plan_t P, int32_t variant) {
     if (!P || (variant != STENCIL_VARIANT_FUSED && variant != STENCIL_VARIANT_PLAIN &&
-               variant != STENCIL_VARIANT_FUSED_PER_PASS)) {
+               variant != STENCIL_VARIANT_FUSED_PER_PASS && variant != STENCIL_VARIANT_TESSELLATE)) {
         set_error("invalid plan or variant");
         return STENCIL_ERR_INVALID_ARG;
     }
@@ -344,9 +365,26 @@ stencil_status_t stencil_plan_get_tile_rows(stencil_plan_t P, int32_t *rows) {
     return STENCIL_OK;
 }
 
+stencil_status_t stencil_plan_set_block_warps(stencil_plan_t P, int32_t warps) {
+    if (!P || warps < 0 || warps > 8) { set_error("invalid plan or block size (0..8 warps)"); return STENCIL_ERR_INVALID_ARG; }
+    P->block_warps = warps;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_get_block_warps(stencil_plan_t P, int32_t *warps) {
+    if (!P || !warps) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *warps = P->block_warps;
+    return STENCIL_OK;
+}
+
 stencil_status_t stencil_plan_launch_count(stencil_plan_t P, int64_t T, int64_t *launches) {
     if (!P || !launches || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
     if (T == 0) { *launches = 0; return STENCIL_OK; }
+    if (P->variant == STENCIL_VARIANT_TESSELLATE && !P->tuned_plain) {
+        const int h = P->k > 0 ? P->k : 8;
+        *launches = 1 + (T + h - 1) / h * (P->dim + 1);   // the set-up copy, then d + 1 stages per time tile
+        return STENCIL_OK;
+    }
     if (!uses_fused(P)) { *launches = T; return STENCIL_OK; }
     const int k = effective_k(P);
     const int64_t mp = multi_passes(P, k, T);
@@ -356,7 +394,9 @@ stencil_status_t stencil_plan_launch_count(stencil_plan_t P, int64_t T, int64_t 
 
 stencil_status_t stencil_plan_describe(stencil_plan_t P, char *buf, int32_t len) {
     if (!P || !buf || len < 1) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
-    std::string s = uses_fused(P) ? fused_describe(*P, effective_k(P)) : std::string("plain(one step per launch)");
+    std::string s = P->variant == STENCIL_VARIANT_TESSELLATE && !P->tuned_plain
+                        ? "tessellate(d+1 stages per time tile of " + std::to_string(P->k > 0 ? P->k : 8) + " levels)"
+                        : uses_fused(P) ? fused_describe(*P, effective_k(P)) : std::string("plain(one step per launch)");
     strncpy(buf, s.c_str(), (size_t)len - 1);
     buf[len - 1] = 0;
     return STENCIL_OK;
@@ -375,8 +415,14 @@ stencil_status_t stencil_run(stencil_plan_t P, const void *u_in, void *u_out, in
         cudaError_t e = cudaMemcpyAsync(u_out, u_in, P->grid_bytes, cudaMemcpyDeviceToDevice, st);
         return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaMemcpyAsync");
     }
+    // an NVTX range around the enqueueing of the sweep (free without a tool attached)
+    struct NvtxRange {
+        NvtxRange() { nvtxRangePushA("stencil_run"); }
+        ~NvtxRange() { nvtxRangePop(); }
+    } nvtx_range;
     stencil_status_t s = ensure_status_word(P);
     if (s != STENCIL_OK) return s;
+    if (P->variant == STENCIL_VARIANT_TESSELLATE && !P->tuned_plain) return tess_run(P, u_in, u_out, T, st);
     const bool fused = uses_fused(P);
     const int k = fused ? effective_k(P) : 1;
     const int64_t passes = (T + k - 1) / k;
@@ -427,97 +473,57 @@ stencil_status_t stencil_run_host(stencil_plan_t P, const void *h_in, void *h_ou
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
 }
 
-stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void *stream, int32_t *best_k, double *best_ms) {
-    if (!P || T < 1) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
-    const int km = fused_max_k(*P);
-    if (km <= 0 || P->variant == STENCIL_VARIANT_PLAIN) {
-        if (best_k) *best_k = 1;
-        if (best_ms) *best_ms = -1.0;
-        return STENCIL_OK;
+stencil_status_t stencil_run_host_many(stencil_plan_t P, int64_t n, const void *const *h_in, void *const *h_out,
+                                       int64_t T, void *stream) {
+    if (!P || n < 0 || (n > 0 && (!h_in || !h_out)) || T < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    for (int64_t i = 0; i < n; ++i)
+        if (!h_in[i] || !h_out[i]) { set_error("null host buffer"); return STENCIL_ERR_INVALID_ARG; }
+    if (n == 0) return STENCIL_OK;
+    for (int i = 0; i < 4; ++i) {
+        stencil_status_t s = ensure_buf(&P->hm_buf[i], P->grid_bytes);
+        if (s != STENCIL_OK) return s;
     }
-    stencil_status_t s = ensure_buf(&P->hws[0], P->grid_bytes);
-    if (s == STENCIL_OK) s = ensure_buf(&P->hws[1], P->grid_bytes);
-    if (s != STENCIL_OK) return s;
+    if (!P->hm_ready) {
+        for (int i = 0; i < 2; ++i)
+            if (cudaStreamCreateWithFlags(&P->hm_st[i], cudaStreamNonBlocking) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "copy stream creation");
+        for (int i = 0; i < 7; ++i)
+            if (cudaEventCreateWithFlags(&P->hm_ev[i], cudaEventDisableTiming) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "event creation");
+        P->hm_ready = true;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(P->hws[0], 0, P->grid_bytes, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const int saved = P->k, saved_rows = P->tile_rows, saved_variant = P->variant;
-    int bk = 1, brows = saved_rows, bvariant = saved_variant;
-    float bms = 1e30f;
-    bool best_plain = false;
-    // tile heights tried in 2D: the default and a few fixed heights below
-    // the grid's row count (duplicates of the clamped maximum are skipped)
-    std::vector<int> rows_c = {0};
-    if (P->dim == 2)
-        for (int r : {32, 48, 64, 96, 128, 192})
-            if (r < P->n[1]) rows_c.push_back(r);
-    if (P->dim == 3)
-        for (int r : {16, 32, 48, 64})
-            if (r < P->n[0]) rows_c.push_back(r);
-    if (P->dim == 1)
-        for (int r : {2, 4, 8, 16, 32})
-            if (r * 128 < P->n[2]) rows_c.push_back(r);
-    // candidates: the one-step kernel (k = 0 here), then every fused depth,
-    // one launch per pass (default tiles) and -- where the grid allows it --
-    // the persistent multi-pass launch with each tile length
-    struct Cand { int variant, rows; };
-    for (int k = 0; k <= km && s == STENCIL_OK; ++k) {
-        std::vector<Cand> cands;
-        if (k == 0) {
-            cands.push_back({STENCIL_VARIANT_FUSED, 0});
-        } else {
-            cands.push_back({STENCIL_VARIANT_FUSED_PER_PASS, 0});
-            if (fused_multi_ok(*P, k))
-                for (int r : rows_c) cands.push_back({STENCIL_VARIANT_FUSED, r});
-        }
-        for (size_t ci = 0; ci < cands.size(); ++ci) {
-            P->tuned_plain = (k == 0);
-            P->k = k == 0 ? 1 : k;
-            P->variant = cands[ci].variant;
-            P->tile_rows = cands[ci].rows;
-            s = stencil_run(P, P->hws[0], P->hws[1], T, stream);   // warm-up
-            if (s != STENCIL_OK) break;
-            float best_rep = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, st);
-                s = stencil_run(P, P->hws[0], P->hws[1], T, stream);
-                cudaEventRecord(e1, st);
-                if (s != STENCIL_OK) break;
-                e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) { s = cuda_fail(e, "tuning run"); break; }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                best_rep = std::min(best_rep, ms);
-            }
-            if (s != STENCIL_OK) break;
-            if (best_rep < bms) {
-                bms = best_rep;
-                bk = k == 0 ? 1 : k;
-                best_plain = (k == 0);
-                brows = cands[ci].rows;
-                bvariant = k == 0 ? saved_variant : cands[ci].variant;
-            }
-        }
+    cudaStream_t s_in = P->hm_st[0], s_out = P->hm_st[1];
+    // events per buffer slot b: input copied (0,1), computed (2,3), output copied (4,5); 6: start
+    cudaEvent_t *ev = P->hm_ev;
+    cudaError_t e = cudaEventRecord(ev[6], st);   // the copies follow the caller's earlier work on `stream`
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev[6], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev[6], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    for (int64_t i = 0; i < n; ++i) {
+        const int b = (int)(i & 1);
+        void *din = P->hm_buf[b], *dout = P->hm_buf[2 + b];
+        // input slot b is free once grid i - 2's sweep has read it
+        if (i >= 2) e = cudaStreamWaitEvent(s_in, ev[2 + b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(din, h_in[i], P->grid_bytes, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[b], s_in);
+        // the sweep waits for its input, and for output slot b to be copied out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[b], 0);
+        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(st, ev[4 + b], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "pipelined host run");
+        stencil_status_t s = stencil_run(P, din, dout, T, stream);
+        if (s != STENCIL_OK) return s;
+        e = cudaEventRecord(ev[2 + b], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev[2 + b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_out[i], dout, P->grid_bytes, cudaMemcpyDeviceToHost, s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4 + b], s_out);
+        if (e != cudaSuccess) return cuda_fail(e, "pipelined host run");
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (s != STENCIL_OK) {
-        P->k = saved;
-        P->tile_rows = saved_rows;
-        P->variant = saved_variant;
-        P->tuned_plain = false;
-        return s;
-    }
-    P->k = bk;
-    P->tile_rows = best_plain ? saved_rows : brows;
-    P->variant = bvariant;
-    P->tuned_plain = best_plain;
-    if (best_k) *best_k = best_plain ? 0 : bk;
-    if (best_ms) *best_ms = bms;
-    return STENCIL_OK;
+    // the last copies out complete before `stream` moves on; then wait
+    e = cudaEventRecord(ev[6], s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[6], 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
 }
 
 // Test hook (not in the public header): sets tile `tile`'s pass counter of

@@ -289,6 +289,8 @@ __host__ __device__ __forceinline__ TileSpan tile_span(int lo, int hi, int n, in
 
 __host__ __device__ constexpr int round_up_c(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ constexpr int max_c(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
 
 __device__ __forceinline__ int64_t wrap_idx(int64_t i, int64_t n) {
     int64_t m = i % n;

@@ -12,10 +12,12 @@
 // sums) into per-block FP64 partials that persist across the steps; a final
 // one-block kernel sums the partials in a fixed order.
 //
-// Forward states are recomputed from checkpoints taken every `ckpt_every`
-// steps: the forward sweep (fused kernels) stores u_0, u_c, u_2c, ...; each
-// backward segment recomputes its c states with the one-step kernel, then
-// runs its c backward steps.
+// Forward states come from checkpoints taken while the forward sweep runs
+// (stencil_run_checkpointed: the fused sweep in segments of c steps, each
+// segment's result kept): the backward sweep walks the segments last to
+// first, recomputes a segment's c - 1 inner states from its checkpoint one
+// step per launch, then runs its c transposed steps.  stencil_adjoint_run
+// takes the checkpoints itself first.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -118,13 +120,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_step_kernel(const __grid_
         for (int v = 0; v < ADJ_VX; ++v)
             if (x0 + v < n2) out[x0 + v] = acc[v];
     }
-    // block sums of the weight-gradient terms (warp tree in FP32, warps in FP64)
+    // block sums of the weight-gradient terms: each thread's FP32 sum over
+    // its own points of this step, then FP64 from the warp tree up
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        float v = gw[j];
-        for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
-        if (lane == 0) red[warp][j] = (double)v;
+        double v = (double)gw[j];
+        for (int o = 16; o > 0; o >>= 1) v = v + __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = v;
     }
     __syncthreads();
     if (threadIdx.x < NP) {
@@ -263,16 +266,17 @@ __global__ void __launch_bounds__(ADJ_THREADS, adj_min_blocks(D, R, PAT)) adjoin
             }
         }
     }
-    // block sums of the weight-gradient terms, fixed order: the warp tree in
-    // FP32 (each lane's term is already an FP32 sum; a 32-lane FP64 tree
-    // would occupy the FP64 pipe -- 2 operations per clock per SM -- for a
-    // third of the kernel), the warps' sums and the running partials in FP64
+    // block sums of the weight-gradient terms, fixed order: each thread's
+    // FP32 sum over its own points of this step (a few dozen products: FP64
+    // per product would keep the FP64 pipe -- 2 operations per clock per SM
+    // on this GPU -- busy for longer than the whole step), then FP64 from the
+    // warp tree up, across warps, blocks and steps
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        float v = gw[j];
-        for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
-        if (lane == 0) red[warp][j] = (double)v;
+        double v = (double)gw[j];
+        for (int o = 16; o > 0; o >>= 1) v = v + __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = v;
     }
     __syncthreads();
     if (tid < NP) {
@@ -354,20 +358,44 @@ static cudaError_t launch_adj(const stencil_plan_s &P, const AdjParams &p, const
 
 using namespace sg;
 
-extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0, const void *grad_uT, int64_t T,
-                                                int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream) {
-    if (!P || !u0 || !grad_uT || !grad_u0 || !grad_w || T < 0) {
-        set_error("invalid argument");
-        return STENCIL_ERR_INVALID_ARG;
-    }
+namespace sg {
+
+static stencil_status_t adj_check(const stencil_plan_s *P, int64_t T, int32_t c) {
     if (P->dtype != STENCIL_F32 || P->r > 2) {
         set_error("the adjoint supports F32 plans of radius 1 or 2");
         return STENCIL_ERR_UNSUPPORTED;
     }
-    if (T > 0 && (ckpt_every < 1 || ckpt_every > T)) {
+    if (T > 0 && (c < 1 || c > T)) {
         set_error("ckpt_every must be in 1..T");
         return STENCIL_ERR_INVALID_ARG;
     }
+    return STENCIL_OK;
+}
+
+// the forward sweep in segments of c steps, segment m's result stored as
+// checkpoint m (m < M - 1) or u_T (the last)
+static stencil_status_t forward_ckpt(stencil_plan_s *P, const void *u0, void *uT, int64_t T, int c, void *ckpts,
+                                     void *stream) {
+    const size_t gb = P->grid_bytes;
+    const int64_t M = (T + c - 1) / c;
+    const void *src = u0;
+    for (int64_t m = 0; m < M; ++m) {
+        void *dst = m == M - 1 ? uT : static_cast<void *>(static_cast<char *>(ckpts) + (size_t)m * gb);
+        const int64_t steps = std::min<int64_t>(c, T - m * c);
+        stencil_status_t s = stencil_run(P, src, dst, steps, stream);
+        if (s != STENCIL_OK) return s;
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+// The backward sweep from checkpoints (u0 = checkpoint 0, ckpts[m - 1] =
+// the state after m c steps): each segment, last to first, recomputes its
+// c - 1 inner states one step per launch (the plan's fused kernels at k = 1)
+// and then runs its c transposed steps.
+static stencil_status_t backward_from_ckpts(stencil_plan_s *P, const void *u0, const void *ckpts,
+                                            const void *grad_uT, int64_t T, int c, void *grad_u0, double *grad_w,
+                                            void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t gb = P->grid_bytes;
     if (T == 0) {
@@ -376,10 +404,9 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
         if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
         return STENCIL_OK;
     }
-    const int c = ckpt_every;
-    const int64_t M = (T + c - 1) / c;   // segments
-    // workspace: checkpoints 1..M-1, c-1 recomputed states, two lam grids
-    const size_t ngrids = (size_t)(M - 1) + (size_t)(c - 1) + 2;
+    const int64_t M = (T + c - 1) / c;
+    // workspace: c - 1 recomputed states, two lam grids, the partials
+    const size_t ngrids = (size_t)(c - 1) + 2;
     const AdjShape shape = adj_shape(*P);
     const int nblocks = shape.nblocks;
     const size_t need = ngrids * gb + 256 + sizeof(double) * (size_t)nblocks * P->np + sizeof(int) * P->np;
@@ -401,15 +428,11 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
     std::vector<int> h_e2c(P->eval_to_compact, P->eval_to_compact + P->np);
     cudaError_t e = cudaMemcpyAsync(e2c, h_e2c.data(), sizeof(int) * P->np, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
-    // checkpoint m lives at grid m-1 (m >= 1); u0 is checkpoint 0
-    auto ckpt = [&](int64_t m) -> const void * { return m == 0 ? u0 : grid_at((size_t)(m - 1)); };
-    auto seg = [&](int i) -> void * { return grid_at((size_t)(M - 1) + (size_t)(i - 1)); };   // i = 1..c-1
-    void *lam[2] = {grid_at((size_t)(M - 1) + (size_t)(c - 1)), grid_at((size_t)(M - 1) + (size_t)c)};
-    // forward: checkpoints
-    for (int64_t m = 1; m < M; ++m) {
-        stencil_status_t s = stencil_run(P, ckpt(m - 1), grid_at((size_t)(m - 1)), c, stream);
-        if (s != STENCIL_OK) return s;
-    }
+    auto ckpt = [&](int64_t m) -> const void * {
+        return m == 0 ? u0 : static_cast<const void *>(static_cast<const char *>(ckpts) + (size_t)(m - 1) * gb);
+    };
+    auto seg = [&](int i) -> void * { return grid_at((size_t)(i - 1)); };   // i = 1..c-1
+    void *lam[2] = {grid_at((size_t)(c - 1)), grid_at((size_t)c)};
     AdjParams p;
     p.n0 = P->n[0];
     p.n1 = P->n[1];
@@ -423,11 +446,10 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
     bool first = true;
     for (int64_t m = M - 1; m >= 0; --m) {
         const int64_t t0 = m * c, t1 = std::min<int64_t>(T, t0 + c);
-        // recompute u_{t0+1} .. u_{t1-1} with one step per launch
         for (int64_t t = t0 + 1; t < t1; ++t) {
             const void *src = (t - 1 == t0) ? ckpt(m) : seg((int)(t - 1 - t0));
-            e = launch_plain(*P, src, seg((int)(t - t0)), st);
-            if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
+            stencil_status_t s = stencil_run(P, src, seg((int)(t - t0)), 1, stream);
+            if (s != STENCIL_OK) return s;
         }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             p.u = static_cast<const float *>(t == t0 ? ckpt(m) : seg((int)(t - t0)));
@@ -447,4 +469,61 @@ extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return STENCIL_ERR_CUDA; }
     return STENCIL_OK;
+}
+
+}  // namespace sg
+
+extern "C" stencil_status_t stencil_run_checkpointed(stencil_plan_t P, const void *u0, void *u_T, int64_t T,
+                                                     int32_t ckpt_every, void *ckpts, void *stream) {
+    if (!P || !u0 || !u_T || T < 0 || (T > ckpt_every && !ckpts)) {
+        set_error("invalid argument");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    stencil_status_t s = adj_check(P, T, ckpt_every);
+    if (s != STENCIL_OK) return s;
+    if (T == 0) return stencil_run(P, u0, u_T, 0, stream);
+    return forward_ckpt(P, u0, u_T, T, ckpt_every, ckpts, stream);
+}
+
+extern "C" stencil_status_t stencil_adjoint_from_checkpoints(stencil_plan_t P, const void *u0, const void *ckpts,
+                                                             const void *grad_uT, int64_t T, int32_t ckpt_every,
+                                                             void *grad_u0, double *grad_w, void *stream) {
+    if (!P || !u0 || !grad_uT || !grad_u0 || !grad_w || T < 0 || (T > ckpt_every && !ckpts)) {
+        set_error("invalid argument");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    stencil_status_t s = adj_check(P, T, ckpt_every);
+    if (s != STENCIL_OK) return s;
+    return backward_from_ckpts(P, u0, ckpts, grad_uT, T, ckpt_every, grad_u0, grad_w, stream);
+}
+
+extern "C" stencil_status_t stencil_adjoint_run(stencil_plan_t P, const void *u0, const void *grad_uT, int64_t T,
+                                                int32_t ckpt_every, void *grad_u0, double *grad_w, void *stream) {
+    if (!P || !u0 || !grad_uT || !grad_u0 || !grad_w || T < 0) {
+        set_error("invalid argument");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    stencil_status_t s = adj_check(P, T, ckpt_every);
+    if (s != STENCIL_OK) return s;
+    if (T == 0) return backward_from_ckpts(P, u0, nullptr, grad_uT, 0, 1, grad_u0, grad_w, stream);
+    // checkpoints (and a scratch u_T) in a plan-owned buffer, then the backward sweep
+    const int c = ckpt_every;
+    const int64_t M = (T + c - 1) / c;
+    const size_t need = (size_t)M * P->grid_bytes;
+    if (P->ckpt_ws_bytes < need) {
+        cudaFree(P->ckpt_ws);
+        P->ckpt_ws = nullptr;
+        P->ckpt_ws_bytes = 0;
+        if (cudaMalloc(&P->ckpt_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("checkpoint allocation of " + std::to_string(need) + " bytes failed");
+            return STENCIL_ERR_OOM;
+        }
+        P->ckpt_ws_bytes = need;
+    }
+    void *ck = P->ckpt_ws;
+    void *uT = static_cast<char *>(P->ckpt_ws) + (size_t)(M - 1) * P->grid_bytes;
+    s = forward_ckpt(P, u0, uT, T, c, ck, stream);
+    if (s != STENCIL_OK) return s;
+    return backward_from_ckpts(P, u0, ck, grad_uT, T, c, grad_u0, grad_w, stream);
 }

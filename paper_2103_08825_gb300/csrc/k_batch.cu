@@ -35,7 +35,7 @@
 namespace sg {
 
 constexpr int BT_NW = 4;          // warps per CTA
-constexpr int BT_LY = 64;         // output rows per tile
+constexpr int BT_LY = 64;         // default output rows per tile (stencil_batch_set_config)
 constexpr int BT_MAXW = 25;
 
 template <typename C> struct BatchGrid {
@@ -65,6 +65,7 @@ template <typename C> struct BatchParams {
     const int *dep_list;               // bands (chunks) whose outputs meet its input window
     BatchCtl *ctl;
     int bkind;
+    int ly;                            // output rows per tile
     C bval;
     int *test_skip_publish;            // test hook: never publish this item (host-side fault injection)
 };
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant
         for (int j = 0; j < Sh::npts; ++j) wr[j] = G.w[j];
         using Geo = F2Geo<DT, R, KB>;
         const int64_t xo0 = (int64_t)b * Geo::BW;
-        const int64_t yo0 = (int64_t)c * BT_LY;
-        const int64_t yo1 = yo0 + BT_LY < G.ny ? yo0 + BT_LY : G.ny;
+        const int64_t yo0 = (int64_t)c * p.ly;
+        const int64_t yo1 = yo0 + p.ly < G.ny ? yo0 + p.ly : G.ny;
         const bool vec_ok = (G.nx % Traits<DT>::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
         // tiles are laid out with the band width of k = KB; shorter first
         // passes use the same tiles (their halo is smaller)
@@ -158,10 +159,12 @@ __global__ void __launch_bounds__(BT_NW * 32) batch_kernel(const __grid_constant
 using namespace sg;
 
 struct stencil_batch_s {
-    int n = 0, r = 0, pattern = 0, dtype = 0, bkind = 0, kb = 4;
+    int n = 0, r = 0, pattern = 0, dtype = 0, bkind = 0, kb = 4, ly = BT_LY;
     double bval = 0.0;
     int device = 0, sm_count = 0;
     std::vector<int64_t> ny, nx, T;
+    std::vector<double> wts;          // every member's compact weights (schedule rebuilds)
+    int np = 0;
     std::vector<size_t> bytes;
     void *d_grids = nullptr;          // BatchGrid<C>[n]
     std::vector<unsigned char> h_grids;
@@ -192,7 +195,13 @@ int tile_bw(int dtype, int r, int kb) {
 }
 
 template <int DT>
-stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weights) {
+stencil_status_t build_batch(stencil_batch_s *B);
+
+template <int DT>
+stencil_status_t rebuild_batch(stencil_batch_s *B) { return build_batch<DT>(B); }
+
+template <int DT>
+stencil_status_t build_batch(stencil_batch_s *B) {
     using C = typename Traits<DT>::C;
     const int n = B->n;
     B->grid_desc_size = sizeof(BatchGrid<C>);
@@ -224,10 +233,10 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
         G.passes = (int)((T + B->kb - 1) / B->kb);
         G.k_first = (int)(T - (int64_t)(G.passes - 1) * B->kb);
         G.bands = (G.nx + bw - 1) / bw;
-        G.chunks = (G.ny + BT_LY - 1) / BT_LY;
+        G.chunks = (G.ny + B->ly - 1) / B->ly;
         G.tile_base = (int)tiles;
         tiles += (long long)G.bands * G.chunks;
-        for (int j = 0; j < np; ++j) G.w[j] = conv_w<C>(weights[g].w[order[j]]);
+        for (int j = 0; j < np; ++j) G.w[j] = conv_w<C>(B->wts[(size_t)g * B->np + order[j]]);
         passes[g] = G.passes;
         maxp = std::max(maxp, G.passes);
     }
@@ -260,7 +269,7 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
         G.coff = (int)dep_off.size();
         dep_off.push_back((int)dep_list.size());
         for (int c = 0; c < G.chunks; ++c)
-            add_list((int64_t)c * BT_LY - hy, std::min<int64_t>((int64_t)(c + 1) * BT_LY, G.ny) + hy, G.ny, BT_LY,
+            add_list((int64_t)c * B->ly - hy, std::min<int64_t>((int64_t)(c + 1) * B->ly, G.ny) + hy, G.ny, B->ly,
                      G.chunks, per);
     }
     std::vector<unsigned long long> items;
@@ -285,9 +294,9 @@ stencil_status_t build_batch(stencil_batch_s *B, const stencil_weights_t *weight
     if (e == cudaSuccess && !dep_list.empty())
         e = cudaMemcpy(B->d_dep_list, dep_list.data(), sizeof(int) * dep_list.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_error("batch upload failed"); return STENCIL_ERR_CUDA; }
-    B->ws.assign(n, nullptr);
+    if (B->ws.size() != (size_t)n) B->ws.assign(n, nullptr);
     for (int g = 0; g < n; ++g) {
-        if (passes[g] < 2) continue;   // a single pass reads `in` and writes `out` only
+        if (passes[g] < 2 || B->ws[g]) continue;   // a single pass reads `in` and writes `out` only
         e = cudaMalloc(&B->ws[g], B->bytes[g]);
         if (e != cudaSuccess) { cudaGetLastError(); set_error("batch workspace allocation failed"); return STENCIL_ERR_OOM; }
     }
@@ -310,16 +319,42 @@ cudaError_t launch_batch(stencil_batch_s *B, cudaStream_t st) {
     p.ctl = B->d_ctl;
     p.bkind = B->bkind;
     p.bval = conv_w<C>(B->bval);
+    p.ly = B->ly;
     p.test_skip_publish = B->d_skip;
     const bool box = B->pattern == STENCIL_BOX;
     // the resident-worker bound keeps every dequeued item's dependencies running
     int bps = 0;
-    auto kern = B->r == 1 ? (box ? batch_kernel<DT, 1, STENCIL_BOX, 4> : batch_kernel<DT, 1, STENCIL_STAR, 4>)
-                          : (box ? batch_kernel<DT, 2, STENCIL_BOX, 2> : batch_kernel<DT, 2, STENCIL_STAR, 2>);
+    auto pick = [&](auto k1, auto k2, auto k3, auto k4) { return B->kb == 1 ? k1 : B->kb == 2 ? k2 : B->kb == 3 ? k3 : k4; };
+    auto kern = B->r == 1 ? (box ? pick(batch_kernel<DT, 1, STENCIL_BOX, 1>, batch_kernel<DT, 1, STENCIL_BOX, 2>,
+                                        batch_kernel<DT, 1, STENCIL_BOX, 3>, batch_kernel<DT, 1, STENCIL_BOX, 4>)
+                                 : pick(batch_kernel<DT, 1, STENCIL_STAR, 1>, batch_kernel<DT, 1, STENCIL_STAR, 2>,
+                                        batch_kernel<DT, 1, STENCIL_STAR, 3>, batch_kernel<DT, 1, STENCIL_STAR, 4>))
+                          : (box ? (B->kb == 1 ? batch_kernel<DT, 2, STENCIL_BOX, 1> : batch_kernel<DT, 2, STENCIL_BOX, 2>)
+                                 : (B->kb == 1 ? batch_kernel<DT, 2, STENCIL_STAR, 1> : batch_kernel<DT, 2, STENCIL_STAR, 2>));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BT_NW * 32, 0);
     const int ctas = B->sm_count * std::max(1, bps);
     kern<<<ctas, BT_NW * 32, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+// free the schedule's device arrays and the captured graph (not the workspaces)
+void release_schedule(stencil_batch_s *B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    cudaFree(B->d_grids);
+    cudaFree(B->d_items);
+    cudaFree(B->d_done);
+    cudaFree(B->d_ctl);
+    cudaFree(B->d_dep_off);
+    cudaFree(B->d_dep_list);
+    B->d_grids = nullptr;
+    B->d_items = nullptr;
+    B->d_done = nullptr;
+    B->d_ctl = nullptr;
+    B->d_dep_off = nullptr;
+    B->d_dep_list = nullptr;
 }
 
 cudaError_t enqueue_batch(stencil_batch_s *B, cudaStream_t st) {
@@ -379,12 +414,14 @@ stencil_status_t stencil_batch_create(stencil_batch_t *out, int32_t n, int32_t d
         B->ny.push_back(ny);
         B->nx.push_back(nx);
         B->T.push_back(T[g]);
+        for (int j = 0; j < np; ++j) B->wts.push_back(weights[g].w[j]);
         B->bytes.push_back((size_t)(ny * nx) * dtype_size(dtype));
     }
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e != cudaSuccess) { delete B; set_error("no CUDA device"); return STENCIL_ERR_CUDA; }
-    stencil_status_t s = dtype == STENCIL_F32 ? build_batch<STENCIL_F32>(B, weights) : build_batch<STENCIL_I32>(B, weights);
+    B->np = np;
+    stencil_status_t s = dtype == STENCIL_F32 ? build_batch<STENCIL_F32>(B) : build_batch<STENCIL_I32>(B);
     if (s != STENCIL_OK) { stencil_batch_destroy(B); return s; }
     *out = B;
     return STENCIL_OK;
@@ -394,18 +431,74 @@ stencil_status_t stencil_batch_destroy(stencil_batch_t B) {
     if (!B) return STENCIL_OK;
     cudaSetDevice(B->device);
     cudaDeviceSynchronize();
-    if (B->exec) cudaGraphExecDestroy(B->exec);
-    if (B->graph) cudaGraphDestroy(B->graph);
-    cudaFree(B->d_grids);
-    cudaFree(B->d_items);
-    cudaFree(B->d_done);
-    cudaFree(B->d_ctl);
+    release_schedule(B);
     cudaFree(B->d_skip);
-    cudaFree(B->d_dep_off);
-    cudaFree(B->d_dep_list);
     for (void *w : B->ws) cudaFree(w);
     delete B;
     return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_set_config(stencil_batch_t B, int32_t k, int32_t tile_rows) {
+    if (!B || k < 0 || tile_rows < 0) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    const int kmax = B->r == 1 ? 4 : 2;
+    const int kb = k == 0 ? kmax : k, ly = tile_rows == 0 ? BT_LY : tile_rows;
+    if (kb > kmax || ly < 4 * B->r * kb || ly > (1 << 20)) {
+        set_error("batch k must be 1.." + std::to_string(kmax) + " and tile rows at least 4 r k");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    for (int g = 0; g < B->n; ++g)
+        if (B->T[g] > 65535 * (int64_t)kb) { set_error("a member's step count needs a larger k"); return STENCIL_ERR_UNSUPPORTED; }
+    if (kb == B->kb && ly == B->ly) return STENCIL_OK;
+    cudaDeviceSynchronize();
+    release_schedule(B);
+    B->kb = kb;
+    B->ly = ly;
+    B->last_in.clear();   // the grid table is uploaded again on the next run
+    return B->dtype == STENCIL_F32 ? rebuild_batch<STENCIL_F32>(B) : rebuild_batch<STENCIL_I32>(B);
+}
+
+stencil_status_t stencil_batch_get_config(stencil_batch_t B, int32_t *k, int32_t *tile_rows) {
+    if (!B || !k || !tile_rows) { set_error("null argument"); return STENCIL_ERR_INVALID_ARG; }
+    *k = B->kb;
+    *tile_rows = B->ly;
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_batch_tune(stencil_batch_t B, const void *const *u_in, void *const *u_out, void *stream,
+                                    double *best_ms) {
+    if (!B || !u_in || !u_out) { set_error("invalid argument"); return STENCIL_ERR_INVALID_ARG; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int kmax = B->r == 1 ? 4 : 2;
+    int bk = B->kb, bl = B->ly;
+    float bms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    stencil_status_t s = STENCIL_OK;
+    for (int k = 1; k <= kmax && s == STENCIL_OK; ++k)
+        for (int ly : {32, 64, 128, 256}) {
+            if (ly < 4 * B->r * k) continue;
+            if (stencil_batch_set_config(B, k, ly) != STENCIL_OK) continue;
+            s = stencil_batch_run(B, u_in, u_out, stream);   // warm-up (captures the graph)
+            if (s != STENCIL_OK) break;
+            float best = 1e30f;
+            for (int rep = 0; rep < 3 && s == STENCIL_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                s = stencil_batch_run(B, u_in, u_out, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            }
+            if (s == STENCIL_OK && best < bms) { bms = best; bk = k; bl = ly; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != STENCIL_OK) return s;
+    s = stencil_batch_set_config(B, bk, bl);
+    if (best_ms) *best_ms = bms;
+    return s;
 }
 
 stencil_status_t stencil_batch_run(stencil_batch_t B, const void *const *u_in, void *const *u_out, void *stream) {

@@ -20,19 +20,26 @@ SG_DECL_F2(F16)
 SG_DECL_F2(I32)
 #undef SG_DECL_F2
 
+static bool f2_multi_geom_ok(const stencil_plan_s &P, int k);
+
 int fused2d_max_k(const stencil_plan_s &P) {
-    if (P.dim != 2 || P.r > 2 || P.n[1] > (1ll << 30)) return 0;
+    if (P.dim != 2 || P.r > 3 || P.n[1] > (1ll << 30)) return 0;
+    int km = 0;
     switch (P.dtype) {
-        case STENCIL_F32: return f2_kmax_F32(P.r);
-        case STENCIL_F64: return f2_kmax_F64(P.r);
-        case STENCIL_BF16: return f2_kmax_BF16(P.r);
-        case STENCIL_F16: return f2_kmax_F16(P.r);
-        case STENCIL_I32: return f2_kmax_I32(P.r);
+        case STENCIL_F32: km = f2_kmax_F32(P.r); break;
+        case STENCIL_F64: km = f2_kmax_F64(P.r); break;
+        case STENCIL_BF16: km = f2_kmax_BF16(P.r); break;
+        case STENCIL_F16: km = f2_kmax_F16(P.r); break;
+        case STENCIL_I32: km = f2_kmax_I32(P.r); break;
     }
-    return 0;
+    // depths above 8 run only as the persistent kernel: the grid must allow it
+    while (km > 8 && !f2_multi_geom_ok(P, km)) --km;
+    return km;
 }
 
 cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    // depths above 8 are built only as the persistent kernel: one pass of it
+    if (k > 8) return launch_fused2d_multi(P, src, dst, dst, k, 1, st);
     switch (P.dtype) {
         case STENCIL_F32: return launch_f2_F32(P, src, dst, k, st);
         case STENCIL_F64: return launch_f2_F64(P, src, dst, k, st);
@@ -46,7 +53,10 @@ cudaError_t launch_fused2d(const stencil_plan_s &P, const void *src, void *dst, 
 // The multi-pass kernel needs halos that wrap at most once (periodic) and
 // coordinates, tiles and items that fit its 32-bit arithmetic.
 bool fused2d_multi_ok(const stencil_plan_s &P, int k) {
-    if (P.dim != 2 || k < 1 || k > fused2d_max_k(P)) return false;
+    return P.dim == 2 && k >= 1 && k <= fused2d_max_k(P) && f2_multi_geom_ok(P, k);
+}
+
+static bool f2_multi_geom_ok(const stencil_plan_s &P, int k) {
     const int v = P.dtype == STENCIL_F64 ? 2 : 4;
     const int al = std::max(16 / (int)dtype_size(P.dtype), v);
     const int64_t h = (P.r * k + al - 1) / al * al, w = 32 * v;
@@ -91,12 +101,11 @@ SG_DECL_F3(F16)
 SG_DECL_F3(I32)
 #undef SG_DECL_F3
 
-// 3D: r <= 2; k <= 4 (r = 1) or 2 (r = 2), bounded by the partial planes
-// each lane keeps in registers and by the window's y-halo.
+// 3D: k <= 4 (r = 1), 2 (r = 2 star) or 1 (r = 2 box, r = 3), bounded by
+// the 2r partial planes per level each thread keeps in registers.
 int fused3d_max_k(const stencil_plan_s &P) {
-    if (P.dim != 3 || P.r > 2 || P.n[0] > (1ll << 30) || P.n[1] > (1ll << 30)) return 0;
-    if (P.r == 2) return P.pattern == STENCIL_BOX ? 1 : 2;   // the r = 2 box spills beyond k = 1
-    return 4;
+    if (P.dim != 3 || P.r > 3 || P.n[0] > (1ll << 30) || P.n[1] > (1ll << 30) || P.n[2] > (1ll << 30)) return 0;
+    return P.r == 1 ? 4 : (P.r == 2 && P.pattern == STENCIL_STAR) ? 2 : 1;
 }
 
 cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
@@ -148,7 +157,7 @@ cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *
 }
 
 std::string fused3d_describe(const stencil_plan_s &P, int k) {
-    return "fused3d(z-streamed planes, 16 warps x 2 rows, k=" + std::to_string(k) + ", planes per job=" +
+    return "fused3d(z-streamed planes, 64-row windows of half-warp rows, k=" + std::to_string(k) + ", planes per job=" +
            (P.tile_rows > 0 ? std::to_string(P.tile_rows) : std::string("default")) + ")";
 }
 

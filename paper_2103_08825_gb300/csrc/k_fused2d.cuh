@@ -35,7 +35,8 @@
 
 namespace sg {
 
-constexpr int F2_NW = 4;       // warps per CTA (independent jobs)
+constexpr int F2_NW = 4;       // default warps per CTA (independent jobs); 1..F2_MAXNW at launch
+constexpr int F2_MAXNW = 8;
 constexpr int F2_ROWS = 4;     // rows per TMA stage
 constexpr int F2_STAGES = 4;   // TMA ring depth per warp (3 stages = 12 rows in flight)
 constexpr int F2_PREF = 4;     // rows prefetched in registers (PROD_REG)
@@ -52,9 +53,8 @@ template <int DT, int R, int K> struct F2Geo {
     static constexpr int STAGE_ELEMS = F2_ROWS * W;
     static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(S);
     static constexpr int WARP_SMEM = F2_STAGES * STAGE_BYTES;
-    static constexpr int SMEM = F2_NW * WARP_SMEM + F2_NW * F2_STAGES * 8;
+    static constexpr int WARP_BYTES = WARP_SMEM + F2_STAGES * 8;   // a warp's stages and barriers
     static_assert(BW >= V, "fusion depth too large for the window");
-    static_assert(R <= V, "x-halo must come from the neighbouring lane");
 };
 
 template <typename C> struct F2Params {
@@ -67,7 +67,7 @@ template <typename C> struct F2Params {
     int vec_ok;        // rows and both base pointers allow V-wide vector access
     int *status;
     JobCtl *ctl;       // job tickets (left at zero by the launch's last warp)
-    C w[25];           // evaluation order; up to the r = 2 box
+    C w[49];           // evaluation order; up to the r = 3 box
 };
 
 // Control block of a persistent multi-pass launch: the item ticket, the
@@ -92,7 +92,7 @@ template <typename C> struct F2MpParams {
     MpCtl *ctl;        // ticket, abort flag, exit count
     int *done;         // [tiles]: passes each tile has finished
     int tiles;         // (all left at zero by the launch's last warp)
-    C w[25];
+    C w[49];
 };
 
 // ------------------------------------------------------------ memory helpers
@@ -223,10 +223,11 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     using G = F2Geo<DT, R, K>;
     using Sh = Shape<2, R, PAT>;
     constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, NS = 2 * R;
-    // step unroll: the partial-row slots repeat every 2R rows; the register
-    // prefetch ring (PROD_REG) every F2_PREF rows
-    constexpr int U = F2_U;
-    static_assert(F2_ROWS % U == 0 && F2_U % NS == 0, "unroll");
+    // step unroll: the partial-row slots repeat every 2R rows, the register
+    // prefetch ring (PROD_REG) every F2_PREF rows and the TMA stages every
+    // F2_ROWS rows: U = lcm(2R, F2_PREF) (4 for r <= 2, 12 for r = 3)
+    constexpr int U = lcm_c(NS, F2_PREF);
+    static_assert(U % NS == 0 && U % F2_PREF == 0 && U % F2_ROWS == 0, "unroll");
     constexpr uint32_t FULLM = (1u << V) - 1u;
 
     // row indices fit in 32 bits (checked by the launcher)
@@ -280,8 +281,10 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     int q = 0;                                   // stage index within the job
     const S *srow = stg + slot * G::STAGE_ELEMS + lane * V;
     for (int i0 = 0; i0 < nsp; i0 += U) {
+#pragma unroll
+        for (int ph = 0; ph < U; ++ph) {
         if constexpr (PROD == PROD_TMA) {
-            if ((i0 & (F2_ROWS - 1)) == 0) {
+            if (ph % F2_ROWS == 0) {
                 const bool ok = mbar_wait_bounded(&bars[slot], par);
                 if (__any_sync(0xffffffffu, !ok)) {
                     // give up: wait (bounded, about ten seconds per stage) for
@@ -298,13 +301,12 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                 srow = stg + slot * G::STAGE_ELEMS + lane * V;
             }
         }
-#pragma unroll
-        for (int ph = 0; ph < U; ++ph) {
+        {
             const int i = i0 + ph;
             const int yin = yi0 + i;
             C cur[V];
             if constexpr (PROD == PROD_TMA) {
-                ldsvec<DT>(srow + ((i0 & (F2_ROWS - 1)) + ph) * W, cur);
+                ldsvec<DT>(srow + (ph % F2_ROWS) * W, cur);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) cur[v] = ring[ph % F2_PREF][v];
@@ -326,10 +328,12 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                 C ext[V + 2 * R];
 #pragma unroll
                 for (int v = 0; v < V; ++v) ext[R + v] = cur[v];
+                // the value qq + 1 columns beyond the lane's edge sits in the
+                // lane qq / V + 1 positions away
 #pragma unroll
                 for (int qq = 0; qq < R; ++qq) {
-                    ext[R - 1 - qq] = __shfl_up_sync(0xffffffffu, cur[V - 1 - qq], 1);
-                    ext[R + V + qq] = __shfl_down_sync(0xffffffffu, cur[qq], 1);
+                    ext[R - 1 - qq] = __shfl_up_sync(0xffffffffu, cur[V - 1 - qq % V], qq / V + 1);
+                    ext[R + V + qq] = __shfl_down_sync(0xffffffffu, cur[qq % V], qq / V + 1);
                 }
                 C emit[V];
                 const int s0 = ph % NS;
@@ -391,7 +395,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
             }
         }
         if constexpr (PROD == PROD_TMA) {
-            if (((i0 + U) & (F2_ROWS - 1)) == 0) {
+            if (ph % F2_ROWS == F2_ROWS - 1) {
                 // stage consumed by every lane: refill it with the stage S ahead
                 __syncwarp();
                 if (lane == 0 && q + F2_STAGES < nst) {
@@ -404,16 +408,36 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
                 if (++slot == F2_STAGES) { slot = 0; par ^= 1u; }
             }
         }
+        }
     }
     gst += (uint32_t)nst;
     return true;
 }
 
-// resident CTAs per SM the register allocation must allow, by fusion depth
-template <int K> constexpr int f2_min_blocks() { return K <= 3 ? 6 : K <= 5 ? 5 : K <= 6 ? 4 : 3; }
+// Resident 4-warp CTAs per SM the register allocation must allow.  Up to the
+// partial-row registers of r = 1, k = 8 the measured table by fusion depth;
+// beyond it, what 2r k V partial values (plus about 96 other registers) per
+// thread leave room for; radius 3 (49-term box, 12-step unroll) gets 168 or
+// 255 registers.
+template <int DT, int R, int K> constexpr int f2_min_blocks() {
+    constexpr int pr = K * 2 * R * Traits<DT>::V * (int)(sizeof(typename Traits<DT>::C) / 4);
+    constexpr int regs = round_up_c(pr + 96, 8);
+    return R == 3 ? (pr <= 48 ? 3 : 2)
+         : pr <= 64 ? (K <= 3 ? 6 : K <= 5 ? 5 : K <= 6 ? 4 : 3)
+                    : (65536 / (F2_NW * 32 * regs) < 2 ? 2 : 65536 / (F2_NW * 32 * regs));
+}
+
+// the per-thread register cap those resident CTAs imply (the same cap a
+// 4-warp launch bound would give), so that the kernels can be launched with
+// any block size of 1..F2_MAXNW warps
+template <int DT, int R, int K> constexpr int f2_regcap() {
+    return (65536 / (F2_NW * 32 * f2_min_blocks<DT, R, K>())) / 8 * 8 > 255
+               ? 255
+               : (65536 / (F2_NW * 32 * f2_min_blocks<DT, R, K>())) / 8 * 8;
+}
 
 template <int DT, int R, int PAT, int K, int PROD>
-__global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
+__global__ void __launch_bounds__(F2_MAXNW * 32) __maxnreg__((f2_regcap<DT, R, K>()))
     fused2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F2Params<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
@@ -422,7 +446,8 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S *stg = reinterpret_cast<S *>(smem + warp * G::WARP_SMEM);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F2_NW * G::WARP_SMEM) + warp * F2_STAGES;
+    const int nw = (int)(blockDim.x >> 5);   // warps in this CTA (the launch's block size)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nw * G::WARP_SMEM) + warp * F2_STAGES;
     if constexpr (PROD == PROD_TMA) {
         if (lane == 0) {
             for (int s = 0; s < F2_STAGES; ++s) mbar_init(&bars[s], 1);
@@ -464,7 +489,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
         }
     }
     __syncwarp();
-    if (lane == 0 && worker_exit_is_last(&p.ctl->exited, gridDim.x * F2_NW)) {
+    if (lane == 0 && worker_exit_is_last(&p.ctl->exited, gridDim.x * nw)) {
         p.ctl->ticket = 0ull;
         p.ctl->exited = 0u;
     }
@@ -483,7 +508,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
 // The per-pass tail of the one-launch-per-pass form (warps idle while the
 // last jobs of a pass finish) then occurs once per run.
 template <int DT, int R, int PAT, int K, int PROD>
-__global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
+__global__ void __launch_bounds__(F2_MAXNW * 32) __maxnreg__((f2_regcap<DT, R, K>()))
     fused2d_mp_kernel(const __grid_constant__ CUtensorMap tm_src0, const __grid_constant__ CUtensorMap tm_even,
                       const __grid_constant__ CUtensorMap tm_odd, const __grid_constant__ F2MpParams<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
@@ -493,7 +518,8 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S *stg = reinterpret_cast<S *>(smem + warp * G::WARP_SMEM);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F2_NW * G::WARP_SMEM) + warp * F2_STAGES;
+    const int nw = (int)(blockDim.x >> 5);   // warps in this CTA (the launch's block size)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nw * G::WARP_SMEM) + warp * F2_STAGES;
     if constexpr (PROD == PROD_TMA) {
         if (lane == 0) {
             for (int s = 0; s < F2_STAGES; ++s) mbar_init(&bars[s], 1);
@@ -582,7 +608,7 @@ __global__ void __launch_bounds__(F2_NW * 32, f2_min_blocks<K>())
     // the last warp out leaves the counters at zero for the next launch
     __syncwarp();
     int last = 0;
-    if (lane == 0) last = worker_exit_is_last(&ctl->exited, gridDim.x * F2_NW);
+    if (lane == 0) last = worker_exit_is_last(&ctl->exited, gridDim.x * nw);
     if (__shfl_sync(0xffffffffu, last, 0)) {
         for (int i = lane; i < p.tiles; i += 32) done[i] = 0;
         if (lane == 0) {
@@ -637,6 +663,7 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.dst = dst;
     p.status = P.d_status;
     p.ctl = static_cast<JobCtl *>(P.d_ctr);
+    if (P.np > (int)(sizeof(p.w) / sizeof(p.w[0]))) return cudaErrorInvalidValue;   // weights fit the parameter block
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1];
     if (ny + 4 * R * K + 64 >= (1ll << 31)) return cudaErrorNotSupported;   // rows are 32-bit in the kernel
@@ -651,24 +678,26 @@ cudaError_t launch_f2_t(const stencil_plan_s &P, const void *src, void *dst, cud
         tma = make_tmap(&map, DT, 2, dims, box, src);
     }
     auto kern = tma ? fused2d_kernel<DT, R, PAT, K, PROD_TMA> : fused2d_kernel<DT, R, PAT, K, PROD_REG>;
-    const int smem = tma ? G::SMEM : 0;
+    const int nw = P.block_warps > 0 ? P.block_warps : F2_NW;
+    const int smem = tma ? nw * G::WARP_BYTES : 0;
     static bool attr_done[2] = {false, false};
     if (!attr_done[tma ? 0 : 1]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tma ? F2_MAXNW * G::WARP_BYTES : 0);
         if (e != cudaSuccess) return e;
         attr_done[tma ? 0 : 1] = true;
     }
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F2_NW * 32, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nw * 32, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    const F2Tiling tl = f2_tiling(nx, ny, G::BW, R * K, (int64_t)P.sm_count * bps * F2_NW, 2, P.tile_rows);
+    const F2Tiling tl = f2_tiling(nx, ny, G::BW, R * K, (int64_t)P.sm_count * bps * nw, 2, P.tile_rows);
     p.Ly = tl.Ly;
     p.bands = tl.bands;
     p.jobs = tl.bands * tl.chunks;
-    int64_t grid = (p.jobs + F2_NW - 1) / F2_NW;
+    int64_t grid = (p.jobs + nw - 1) / nw;
     if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;
-    kern<<<(unsigned)grid, F2_NW * 32, smem, st>>>(map, p);
+    kern<<<(unsigned)grid, nw * 32, smem, st>>>(map, p);
     return cudaGetLastError();
 }
 
@@ -690,6 +719,7 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     p.dst_odd = dst_odd;
     p.passes = passes;
     p.status = P.d_status;
+    if (P.np > (int)(sizeof(p.w) / sizeof(p.w[0]))) return cudaErrorInvalidValue;   // weights fit the parameter block
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1];
     const bool al = ((uintptr_t)src0 % 16 == 0) && ((uintptr_t)dst_even % 16 == 0) && ((uintptr_t)dst_odd % 16 == 0);
@@ -704,18 +734,20 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
         for (int i = 0; i < 3 && tma; ++i) tma = make_tmap(&maps[i], DT, 2, dims, box, bases[i]);
     }
     auto kern = tma ? fused2d_mp_kernel<DT, R, PAT, K, PROD_TMA> : fused2d_mp_kernel<DT, R, PAT, K, PROD_REG>;
-    const int smem = tma ? G::SMEM : 0;
+    const int nw = P.block_warps > 0 ? P.block_warps : F2_NW;
+    const int smem = tma ? nw * G::WARP_BYTES : 0;
     static bool attr_done[2] = {false, false};
     if (!attr_done[tma ? 0 : 1]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tma ? F2_MAXNW * G::WARP_BYTES : 0);
         if (e != cudaSuccess) return e;
         attr_done[tma ? 0 : 1] = true;
     }
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F2_NW * 32, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nw * 32, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    const int64_t slots = (int64_t)P.sm_count * bps * F2_NW;
+    const int64_t slots = (int64_t)P.sm_count * bps * nw;
     // about three jobs per resident warp and pass: the next pass's items find
     // their dependencies finished (with one job per warp the passes would
     // run in lock step)
@@ -731,77 +763,83 @@ cudaError_t launch_f2mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     p.ctl = static_cast<MpCtl *>(P.d_mp);
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
     const int64_t jobs = (int64_t)p.tiles * passes;
-    int64_t grid = (jobs + F2_NW - 1) / F2_NW;
+    int64_t grid = (jobs + nw - 1) / nw;
     if (grid > (int64_t)P.sm_count * bps) grid = (int64_t)P.sm_count * bps;
-    kern<<<(unsigned)grid, F2_NW * 32, smem, st>>>(maps[0], maps[1], maps[2], p);
+    kern<<<(unsigned)grid, nw * 32, smem, st>>>(maps[0], maps[1], maps[2], p);
     return cudaGetLastError();
 }
 
-// Largest K instantiated for (dtype, r) -- bounded by register pressure.
+// Largest K instantiated for (dtype, r): bounded by the partial rows a lane
+// keeps in registers (2r per level) and by the window's halo (W - 2H >= V).
+// Depths beyond 8 are built for FP32 and int32 storage (the benchmarked and
+// the bit-exact types); FP64 and the half-precision storage types stop at 8
+// (radius 1), 4 (radius 2) and 2 (radius 3), which keeps the build short.
 template <int DT> constexpr int f2_kmax(int r) {
-    return Traits<DT>::V == 2 ? (r == 1 ? 4 : 2) : (r == 1 ? 8 : 4);
+    return (DT == STENCIL_F32 || DT == STENCIL_I32) ? (r == 1 ? 16 : r == 2 ? 4 : 2)
+                                                    : (r == 1 ? 8 : r == 2 ? 4 : 2);
 }
 
-template <int DT, int R, int PAT>
-cudaError_t launch_f2_k(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
-    constexpr int KM = f2_kmax<DT>(R);
-    switch (k) {
-        case 1: return launch_f2_t<DT, R, PAT, 1>(P, src, dst, st);
-        case 2: return launch_f2_t<DT, R, PAT, 2>(P, src, dst, st);
-        case 3: if constexpr (KM >= 3) return launch_f2_t<DT, R, PAT, 3>(P, src, dst, st); break;
-        case 4: if constexpr (KM >= 4) return launch_f2_t<DT, R, PAT, 4>(P, src, dst, st); break;
-        case 5: if constexpr (KM >= 5) return launch_f2_t<DT, R, PAT, 5>(P, src, dst, st); break;
-        case 6: if constexpr (KM >= 6) return launch_f2_t<DT, R, PAT, 6>(P, src, dst, st); break;
-        case 7: if constexpr (KM >= 7) return launch_f2_t<DT, R, PAT, 7>(P, src, dst, st); break;
-        case 8: if constexpr (KM >= 8) return launch_f2_t<DT, R, PAT, 8>(P, src, dst, st); break;
+// Depths above 8 exist only as the persistent multi-pass kernel; a single
+// pass of such a depth runs as that kernel with one pass.
+constexpr int F2_PER_PASS_KMAX = 8;
+
+// Fusion depths KLO..KHI of one radius and both patterns; each (dtype,
+// radius, depth range) is instantiated in a translation unit of its own, so
+// that the build compiles them in parallel.
+template <int DT, int R, int K, int KHI>
+cudaError_t launch_f2_kr(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    if constexpr (K > KHI || K > f2_kmax<DT>(R) || K > F2_PER_PASS_KMAX) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (k == K)
+            return P.pattern == STENCIL_BOX ? launch_f2_t<DT, R, STENCIL_BOX, K>(P, src, dst, st)
+                                            : launch_f2_t<DT, R, STENCIL_STAR, K>(P, src, dst, st);
+        return launch_f2_kr<DT, R, K + 1, KHI>(P, src, dst, k, st);
     }
-    return cudaErrorInvalidValue;
 }
 
-template <int DT, int R, int PAT>
-cudaError_t launch_f2mp_k(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
-                          cudaStream_t st) {
-    constexpr int KM = f2_kmax<DT>(R);
-    switch (k) {
-        case 1: return launch_f2mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st);
-        case 2: return launch_f2mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st);
-        case 3: if constexpr (KM >= 3) return launch_f2mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
-        case 4: if constexpr (KM >= 4) return launch_f2mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
-        case 5: if constexpr (KM >= 5) return launch_f2mp_t<DT, R, PAT, 5>(P, src0, de, dof, passes, st); break;
-        case 6: if constexpr (KM >= 6) return launch_f2mp_t<DT, R, PAT, 6>(P, src0, de, dof, passes, st); break;
-        case 7: if constexpr (KM >= 7) return launch_f2mp_t<DT, R, PAT, 7>(P, src0, de, dof, passes, st); break;
-        case 8: if constexpr (KM >= 8) return launch_f2mp_t<DT, R, PAT, 8>(P, src0, de, dof, passes, st); break;
+template <int DT, int R, int K, int KHI>
+cudaError_t launch_f2mp_kr(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                           cudaStream_t st) {
+    if constexpr (K > KHI || K > f2_kmax<DT>(R)) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (k == K)
+            return P.pattern == STENCIL_BOX ? launch_f2mp_t<DT, R, STENCIL_BOX, K>(P, src0, de, dof, passes, st)
+                                            : launch_f2mp_t<DT, R, STENCIL_STAR, K>(P, src0, de, dof, passes, st);
+        return launch_f2mp_kr<DT, R, K + 1, KHI>(P, src0, de, dof, k, passes, st);
     }
+}
+
+// entry points of the instantiation units: radius 1 depths 1..8 (with the
+// dispatcher), radius 1 depths 9..16, radius 2, radius 3
+template <int DT, int R, int KLO, int KHI>
+cudaError_t launch_f2_range(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    return launch_f2_kr<DT, R, KLO, KHI>(P, src, dst, k, st);
+}
+template <int DT, int R, int KLO, int KHI>
+cudaError_t launch_f2mp_range(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                              cudaStream_t st) {
+    return launch_f2mp_kr<DT, R, KLO, KHI>(P, src0, de, dof, k, passes, st);
+}
+
+// (depths above F2_PER_PASS_KMAX: launch_fused2d runs the persistent kernel)
+template <int DT>
+cudaError_t launch_f2_dt(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    if (k > F2_PER_PASS_KMAX) return cudaErrorNotSupported;
+    if (P.r == 1) return launch_f2_range<DT, 1, 1, 8>(P, src, dst, k, st);
+    if (P.r == 2) return launch_f2_range<DT, 2, 1, 16>(P, src, dst, k, st);
+    if (P.r == 3) return launch_f2_range<DT, 3, 1, 16>(P, src, dst, k, st);
     return cudaErrorInvalidValue;
-}
-
-// One radius, both patterns, every k: each (dtype, radius) is instantiated in
-// a translation unit of its own, so that the build compiles them in parallel.
-template <int DT, int R>
-cudaError_t launch_f2_r(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
-    return P.pattern == STENCIL_BOX ? launch_f2_k<DT, R, STENCIL_BOX>(P, src, dst, k, st)
-                                    : launch_f2_k<DT, R, STENCIL_STAR>(P, src, dst, k, st);
-}
-
-template <int DT, int R>
-cudaError_t launch_f2mp_r(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
-                          cudaStream_t st) {
-    return P.pattern == STENCIL_BOX ? launch_f2mp_k<DT, R, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
-                                    : launch_f2mp_k<DT, R, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
 }
 
 template <int DT>
 cudaError_t launch_f2mp_dt(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
                            cudaStream_t st) {
-    if (P.r == 1) return launch_f2mp_r<DT, 1>(P, src0, de, dof, k, passes, st);
-    if (P.r == 2) return launch_f2mp_r<DT, 2>(P, src0, de, dof, k, passes, st);
-    return cudaErrorInvalidValue;
-}
-
-template <int DT>
-cudaError_t launch_f2_dt(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
-    if (P.r == 1) return launch_f2_r<DT, 1>(P, src, dst, k, st);
-    if (P.r == 2) return launch_f2_r<DT, 2>(P, src, dst, k, st);
+    if (P.r == 1) return k <= 8 ? launch_f2mp_range<DT, 1, 1, 8>(P, src0, de, dof, k, passes, st)
+                                : launch_f2mp_range<DT, 1, 9, 16>(P, src0, de, dof, k, passes, st);
+    if (P.r == 2) return launch_f2mp_range<DT, 2, 1, 16>(P, src0, de, dof, k, passes, st);
+    if (P.r == 3) return launch_f2mp_range<DT, 3, 1, 16>(P, src0, de, dof, k, passes, st);
     return cudaErrorInvalidValue;
 }
 

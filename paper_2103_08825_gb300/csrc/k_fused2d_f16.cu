@@ -1,24 +1,22 @@
-// k_fused2d_f16.cu -- instantiations of the 2D fused kernel for STENCIL_F16
-// storage, radius 1, and the dispatcher (radius 2 is instantiated in
-// k_fused2d_f16_r2.cu: one translation unit each keeps the build parallel).
+// k_fused2d_f16.cu -- the 2D fused kernel for STENCIL_F16 storage: radius 1
+// at fusion depths 1..8, and the dispatcher.  Radii 2 and 3 are instantiated
+// in k_fused2d_f16_r2.cu and _r3.cu (one translation unit each keeps the build
+// parallel); depths above 8 exist only as the persistent kernel.
 #include "k_fused2d.cuh"
 
 namespace sg {
-extern template cudaError_t launch_f2_r<STENCIL_F16, 2>(const stencil_plan_s &, const void *, void *, int,
-                                                          cudaStream_t);
+extern template cudaError_t launch_f2_range<STENCIL_F16, 2, 1, 16>(const stencil_plan_s &, const void *, void *,
+                                                                    int, cudaStream_t);
+extern template cudaError_t launch_f2_range<STENCIL_F16, 3, 1, 16>(const stencil_plan_s &, const void *, void *,
+                                                                    int, cudaStream_t);
 cudaError_t launch_f2_F16(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
     return launch_f2_dt<STENCIL_F16>(P, src, dst, k, st);
 }
 int f2_kmax_F16(int r) { return f2_kmax<STENCIL_F16>(r); }
+// output columns of a band: the 32 V-wide window less an aligned halo each side
 int f2_bw_F16(int r, int k) {
-    switch (k) {
-        case 1: return r == 1 ? F2Geo<STENCIL_F16, 1, 1>::BW : F2Geo<STENCIL_F16, 2, 1>::BW;
-        case 2: return r == 1 ? F2Geo<STENCIL_F16, 1, 2>::BW : F2Geo<STENCIL_F16, 2, 2>::BW;
-        default: {
-            int v = Traits<STENCIL_F16>::V, w = 32 * v, al = align_elems<STENCIL_F16>() > v ? align_elems<STENCIL_F16>() : v;
-            int h = (r * k + al - 1) / al * al;
-            return w - 2 * h;
-        }
-    }
+    const int v = Traits<STENCIL_F16>::V, w = 32 * v;
+    const int al = align_elems<STENCIL_F16>() > v ? align_elems<STENCIL_F16>() : v;
+    return w - 2 * ((r * k + al - 1) / al * al);
 }
 }  // namespace sg

@@ -3,5 +3,6 @@
 #include "k_fused2d.cuh"
 
 namespace sg {
-template cudaError_t launch_f2_r<STENCIL_F32, 2>(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+template cudaError_t launch_f2_range<STENCIL_F32, 2, 1, 16>(const stencil_plan_s &, const void *, void *, int,
+                                                             cudaStream_t);
 }  // namespace sg

@@ -1,0 +1,8 @@
+// k_fused2d_f32_r3.cu -- instantiations of the 2D fused kernel for
+// STENCIL_F32 storage, radius 3 (own translation unit: the build compiles in parallel).
+#include "k_fused2d.cuh"
+
+namespace sg {
+template cudaError_t launch_f2_range<STENCIL_F32, 3, 1, 16>(const stencil_plan_s &, const void *, void *, int,
+                                                             cudaStream_t);
+}  // namespace sg

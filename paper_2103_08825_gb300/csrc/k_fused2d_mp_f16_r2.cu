@@ -1,8 +1,9 @@
-// k_fused2d_mp_f16_r2.cu -- instantiations of the persistent multi-pass 2D kernel
-// for STENCIL_F16 storage, radius 2 (own translation unit: the build compiles in parallel).
+// k_fused2d_mp_f16_r2.cu -- instantiations of the persistent multi-pass 2D
+// kernel for STENCIL_F16 storage, radius 2 (own translation unit: the build
+// compiles in parallel).
 #include "k_fused2d.cuh"
 
 namespace sg {
-template cudaError_t launch_f2mp_r<STENCIL_F16, 2>(const stencil_plan_s &, const void *, void *, void *, int, int,
-                                                     cudaStream_t);
+template cudaError_t launch_f2mp_range<STENCIL_F16, 2, 1, 16>(const stencil_plan_s &, const void *, void *,
+                                                               void *, int, int, cudaStream_t);
 }  // namespace sg

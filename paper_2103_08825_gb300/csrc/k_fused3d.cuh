@@ -3,28 +3,37 @@
 //
 // The paper's time-loop unroll-and-jam (Section 3.3, Algorithm 1) advances a
 // vector set k levels while it streams past, keeping older levels in
-// registers; its tiling (Section 3.4) extends the same scheme to 2D and 3D
-// because only the unit-stride dimension is special.  Here a CTA owns an
-// xy window of (W x WY) points and streams the planes of a z range:
+// registers ("vrl"); its tiling (Section 3.4) extends the scheme to 2D and 3D.
+// Here a CTA owns an xy window of W x WY points and streams the planes of a z
+// range through it:
 //
-//   threads   16 warps stacked in y, each warp RY = 2 rows of the window,
-//             each lane V contiguous x values of those rows;
+//   threads   16 warps; each half-warp (16 lanes x V contiguous values = W
+//             columns) owns RY consecutive rows of the window, so a warp holds
+//             2 RY rows and the CTA 32 RY;
 //   levels    every incoming plane of level s adds its terms to the 2r
 //             partial planes of level s+1 it touches (registers); the plane
 //             that receives its last term is emitted as level s+1's input;
-//   in-plane  x-neighbours by warp shuffle; y-neighbours inside a warp are in
-//             registers, the r rows beyond a warp's edges are exchanged with
-//             the warps above and below through shared memory (one barrier
-//             per level); level-0 planes are read straight from the stage;
-//   input     PROD_TMA: warp 0 lane 0 loads whole window planes with 3D TMA
-//             into an 8-stage ring (mbarrier completion, bounded waits);
-//             PROD_CPASYNC: every thread copies its share of the plane with
+//   in-plane  x-neighbours by shuffles within the half-warp; y-neighbours
+//             from shared memory: level-0 rows straight from the TMA stage,
+//             level s+1 rows from an exchange plane every half-warp writes
+//             its emitted rows into (one CTA barrier per level);
+//   input     PROD3_TMA: one thread loads whole window planes with 3D TMA
+//             into a 6-stage ring (mbarrier completion, bounded waits);
+//             PROD3_CPASYNC: every thread copies its share of the plane with
 //             cp.async, indices wrapped (periodic grids, unaligned rows);
-//   halo      the window's outer H >= rK columns and rK rows are recomputed
-//             (overlapped tiling); a z range reads rK planes each side;
+//   tiling    overlapped (the window recomputes an r k halo), but on a
+//             Dirichlet grid a window never extends past the domain: the
+//             first tile of an axis starts at 0 and the last ends at n, so the
+//             boundary side needs no recomputed halo -- its neighbours are the
+//             boundary value.  Interior tiles carry H >= r k halo columns
+//             (16-byte aligned for TMA) and r k halo rows each side;
 //   order     one multiply then FMAs in lexicographic (o_z, o_y, o_x) order,
 //             identical to the plain kernel: every K is bit-identical.
 #pragma once
+
+#include <string.h>
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "k_fused2d.cuh"
@@ -32,41 +41,94 @@
 
 namespace sg {
 
-constexpr int F3_NWY = 16;               // warps per CTA, stacked in y
-constexpr int F3_RY = 2;                 // window rows per warp
-constexpr int F3_WY = F3_NWY * F3_RY;    // window rows
-constexpr int F3_STAGES = 8;             // plane ring depth: ~112 KiB in flight per SM
-constexpr int F3_THREADS = F3_NWY * 32;
+constexpr int F3_NW = 16;                // warps per CTA
+constexpr int F3_THREADS = F3_NW * 32;
+constexpr int F3_LX = 16;                // lanes along x: a half-warp spans the window's width
+constexpr int F3_STAGES = 6;             // plane ring depth (TMA)
 enum { PROD3_TMA = 0, PROD3_CPASYNC = 1 };
 
-template <int DT, int R, int K> struct F3Geo {
+template <int DT, int R, int K, int RY> struct F3Geo {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
     static constexpr int V = Traits<DT>::V;
-    static constexpr int W = 32 * V;
+    static constexpr int W = F3_LX * V;                              // window columns
+    static constexpr int WY = 2 * F3_NW * RY;                        // window rows
     static constexpr int AL = max_c(align_elems<DT>(), V);
-    static constexpr int H = round_up_c(R * K, AL);
-    static constexpr int BW = W - 2 * H;
-    static constexpr int HY = R * K;
-    static constexpr int BY = F3_WY - 2 * HY;
-    static constexpr int PLANE = W * F3_WY;
+    static constexpr int H = round_up_c(R * K, AL);                  // x halo of an interior tile
+    static constexpr int HY = R * K;                                 // y halo
+    static constexpr int PLANE = W * WY;
     static constexpr int STAGE_BYTES = PLANE * (int)sizeof(S);
-    static constexpr int XROWS = 2 * R;                              // edge rows a warp publishes
-    static constexpr int XBUF_BYTES = 2 * F3_NWY * XROWS * W * (int)sizeof(C);
+    static constexpr int XBUF_BYTES = 2 * PLANE * (int)sizeof(C);    // exchange plane, double-buffered
     static constexpr int SMEM = F3_STAGES * STAGE_BYTES + XBUF_BYTES + F3_STAGES * 8;
-    static_assert(BW >= V && BY >= 1, "fusion depth too large for the window");
-    static_assert(R <= V && R <= F3_RY, "halo must come from the neighbouring lane / warp");
+    static_assert(W - 2 * H >= V && WY - 2 * HY >= 1, "fusion depth too large for the window");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
+
+// Tiling of one axis.  bnd (a Dirichlet axis longer than the window): tile 0
+// outputs [0, F) from the window [0, W); tiles 1 .. T-2 output B = W - 2H
+// values each from a window starting H before their output; tile T-1 outputs
+// the rest, up to n, from the window [n - W, n).  Otherwise uniform tiles of
+// B values with windows starting `lo` before their output (H when periodic,
+// 0 for a Dirichlet axis no longer than the window, which is one tile).
+struct F3Axis {
+    int n, W, H, T, F, B, lo, bnd;
+};
+
+inline F3Axis f3_axis(int64_t n, int W, int H, bool dirichlet) {
+    F3Axis a{(int)n, W, H, 1, 0, W - 2 * H, H, 0};
+    if (dirichlet && n > W) {
+        a.bnd = 1;
+        a.F = W - H;
+        a.T = n <= 2 * a.F ? 2 : 2 + (int)((n - 2 * a.F + a.B - 1) / a.B);
+        a.lo = H;
+    } else if (dirichlet) {
+        a.T = 1;
+        a.B = (int)n;
+        a.lo = 0;
+    } else {
+        a.T = (int)((n + a.B - 1) / a.B);
+    }
+    return a;
+}
+
+// output range [os, oe) and window start ws of tile t
+__host__ __device__ __forceinline__ void f3_tile(const F3Axis &a, int t, int &os, int &oe, int &ws) {
+    if (a.bnd) {
+        os = t == 0 ? 0 : a.F + (t - 1) * a.B;
+        oe = t == a.T - 1 ? a.n : a.F + t * a.B;
+        ws = t == 0 ? 0 : (t == a.T - 1 ? a.n - a.W : os - a.H);
+    } else {
+        os = t * a.B;
+        oe = os + a.B < a.n ? os + a.B : a.n;
+        ws = os - a.lo;
+    }
+}
+
+// The tiles whose outputs meet the coordinate range [lo, hi) (wrapped on a
+// periodic axis; requires -n <= lo and hi <= 2n).
+__host__ __device__ __forceinline__ TileSpan f3_span(const F3Axis &a, int lo, int hi, bool periodic) {
+    if (!a.bnd) return tile_span(lo, hi, a.n, a.B, periodic);
+    TileSpan s{0, 0, 0, 0, 0, 0};
+    const int c0 = lo > 0 ? lo : 0, c1 = hi < a.n ? hi : a.n;
+    if (c0 >= c1) return s;
+    const int t0 = c0 < a.F ? 0 : 1 + (c0 - a.F) / a.B;
+    const int t1 = c1 - 1 < a.F ? 0 : 1 + (c1 - 1 - a.F) / a.B;
+    s.a0 = t0 < a.T - 1 ? t0 : a.T - 1;
+    s.n0 = (t1 < a.T - 1 ? t1 : a.T - 1) + 1 - s.a0;
+    return s;
+}
 
 template <typename C> struct F3Params {
     GridGeom<C> g;          // n0 = nz, n1 = ny, n2 = nx
     const void *src;
     void *dst;
-    int64_t jobs, tiles_x, tiles_y, Lz;
+    F3Axis ax, ay;
+    int chunks, Lz;
+    long long jobs;
     int vec_ok;
     int *status;
     JobCtl *ctl;            // job tickets (left at zero by the launch's last CTA)
-    C w[125];               // evaluation order; up to the r = 2 box
+    C w[kMaxPts];           // evaluation order (read from the constant bank)
 };
 
 template <typename C> struct F3MpParams {
@@ -75,13 +137,14 @@ template <typename C> struct F3MpParams {
     void *dst_even;         // output of the passes p with (passes - 1 - p) even (includes the last)
     void *dst_odd;
     int passes;
-    int tiles_x, tiles_y, chunks, Lz;
+    F3Axis ax, ay;
+    int chunks, Lz;
     int vec_ok;
     int *status;
     MpCtl *ctl;             // ticket, abort flag, exit count
     int *done;              // [tiles]: passes each tile has finished
     int tiles;              // (all left at zero by the launch's last CTA)
-    C w[125];
+    C w[kMaxPts];
 };
 
 // V arithmetic values (16 or 32 bytes) to / from shared memory, 16-byte accesses
@@ -97,9 +160,6 @@ template <typename C, int V> __device__ __forceinline__ void ld_shared_vec(const
         reinterpret_cast<uint4 *>(v)[i] = reinterpret_cast<const uint4 *>(p)[i];
 }
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
-}
 __device__ __forceinline__ void cp_async16(void *smem, const void *g) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
 }
@@ -109,19 +169,17 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Copy window plane z (virtual, wrapped or boundary) into a stage, every
-// thread a share, with cp.async (4-byte elements) or plain stores of the
-// boundary value.  Used for periodic grids and rows TMA cannot address.  A
+// thread a share, with 16-byte cp.async copies where a chunk is aligned and
+// L2 loads element by element elsewhere, or stores of the boundary value.  Used for periodic grids and rows TMA cannot address.  A
 // thread copies the same 16-byte column chunk of several rows; a chunk that
 // lies outside a periodic grid is wrapped by one extent, and when the grid's
 // rows are 16-byte multiples it is still one aligned 16-byte copy.
-template <int DT>
+template <int DT, int W, int WY>
 __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, const typename Traits<DT>::S *src,
                                                  int64_t nx, int64_t ny, int64_t nz, bool periodic,
                                                  typename Traits<DT>::C bval, int64_t xw0, int64_t yw0, int64_t z,
                                                  bool vec_ok) {
     using S = typename Traits<DT>::S;
-    using G = F3Geo<DT, 1, 1>;
-    constexpr int W = G::W;
     constexpr int VE = 16 / (int)sizeof(S);   // elements per 16-byte copy
     constexpr int TPR = W / VE;               // threads per window row
     constexpr int RSTEP = F3_THREADS / TPR;   // rows per sweep of the block
@@ -137,12 +195,11 @@ __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, 
         xin = xs >= 0 && xs + VE <= nx;
     }
     const bool fast = vec_ok && xin;
-    for (int row = (int)(threadIdx.x / TPR); row < F3_WY; row += RSTEP) {
+    for (int row = (int)(threadIdx.x / TPR); row < WY; row += RSTEP) {
         int64_t y = yw0 + row;
         bool yin = y >= 0 && y < ny;
         if (!yin && periodic) {
-            y = y < 0 ? y + ny : y - ny;
-            if (y < 0 || y >= ny) y = wrap_idx(y, ny);
+            y = wrap_idx(y, ny);
             yin = true;
         }
         S *d = stage + row * W + col;
@@ -155,59 +212,87 @@ __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, 
         if (fast) {
             cp_async16(d, rowp + xs);
         } else {
+            // element by element through L2 (ld.global.cg): within a
+            // persistent launch other SMs wrote these values, so no copy may
+            // come from a stale L1 line
 #pragma unroll
             for (int q = 0; q < VE; ++q) {
-                int64_t x = x0 + q;
-                if (x >= 0 && x < nx) {
-                    if constexpr (sizeof(S) >= 4) cp_async4(d + q, rowp + x);
-                    else d[q] = rowp[x];
-                } else if (periodic) {
-                    if constexpr (sizeof(S) >= 4) cp_async4(d + q, rowp + wrap_idx(x, nx));
-                    else d[q] = rowp[wrap_idx(x, nx)];
-                } else {
-                    d[q] = from_c<S>(bval);
-                }
+                const int64_t x = x0 + q;
+                if (x >= 0 && x < nx) d[q] = __ldcg(rowp + x);
+                else if (periodic) d[q] = __ldcg(rowp + wrap_idx(x, nx));
+                else d[q] = from_c<S>(bval);
             }
         }
     }
 }
 
-// One job: the output tile [xo0, xo0+BW) x [yo0, yo0+BY) for planes
-// [zo0, zo1).  MASK: the window touches a Dirichlet boundary, so out-of-domain
-// cells are reset at every level.  Returns false if a bounded wait gave up.
-template <int DT, int R, int PAT, int K, int PROD, bool MASK>
+// x-neighbours of a lane's V values: ext[R + v] = x[v], ext[R - 1 - q] the
+// value q + 1 columns left of the lane's first column, ext[R + V + q] the
+// value q + 1 columns right of its last, taken from the lane q / V + 1
+// positions away within the half-warp.  Lanes at the half-warp's edge get
+// their own value there (window-edge halo: garbage that never reaches a stored
+// output, or -- MASK -- replaced by the boundary value when that column lies
+// outside the domain).
+template <typename C, int V, int R, bool MASK>
+__device__ __forceinline__ void x_extend(const C *x, C *ext, const bool *lout, const bool *rout, C bval) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) ext[R + v] = x[v];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int d = q / V + 1;
+        C l = __shfl_up_sync(0xffffffffu, x[V - 1 - q % V], d, F3_LX);
+        C r = __shfl_down_sync(0xffffffffu, x[q % V], d, F3_LX);
+        if constexpr (MASK) {
+            l = lout[q] ? bval : l;
+            r = rout[q] ? bval : r;
+        }
+        ext[R - 1 - q] = l;
+        ext[R + V + q] = r;
+    }
+}
+
+// One job: the output tile [osx, oex) x [osy, oey) x [zo0, zo1) from the
+// window columns [wsx, wsx + W) and rows [wsy, wsy + WY), streaming the planes
+// zo0 - rK .. zo1 + rK - 1.  MASK: the job reaches the Dirichlet boundary, so
+// cells and window-edge neighbours outside the domain take the boundary value
+// at every level.  Returns false if a bounded wait gave up.
+template <int DT, int R, int PAT, int K, int RY, int PROD, bool MASK>
 __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typename Traits<DT>::S *__restrict__ src,
-                                            typename Traits<DT>::S *__restrict__ dst, int64_t nx, int64_t ny,
-                                            int64_t nz, bool dir, typename Traits<DT>::C bval,
-                                            const typename Traits<DT>::C *wr, int64_t xo0, int64_t yo0,
-                                            int64_t zo0, int64_t zo1, bool vec_ok, typename Traits<DT>::S *stages,
-                                            typename Traits<DT>::C *xbuf, uint64_t *bars, uint32_t &gst, int &xpar,
-                                            int lane, int warp) {
+                                            typename Traits<DT>::S *__restrict__ dst, int nx, int ny, int nz,
+                                            bool dir, typename Traits<DT>::C bval, const typename Traits<DT>::C *wr,
+                                            int wsx, int osx, int oex, int wsy, int osy, int oey, int zo0, int zo1,
+                                            bool vec_ok, typename Traits<DT>::S *stages, typename Traits<DT>::C *xbuf,
+                                            uint64_t *bars, uint32_t &gst, int &xpar, int lane, int warp) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    using G = F3Geo<DT, R, K>;
+    using G = F3Geo<DT, R, K, RY>;
     using Sh = Shape<3, R, PAT>;
-    constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, HY = G::HY, BY = G::BY;
-    constexpr int RY = F3_RY, NS = 2 * R, NR = RY + 2 * R;   // NR: rows incl. y-halo
-    constexpr int U = NS;                                    // z unroll: partial-plane slots repeat every 2R
+    constexpr int V = G::V, W = G::W, WY = G::WY, PLANE = G::PLANE;
+    constexpr int NS = 2 * R, NR = RY + 2 * R;   // NR: rows a half-warp reads, with the y-halo
+    constexpr int U = NS;                        // z unroll: partial-plane slots repeat every 2R
     constexpr uint32_t FULLM = (1u << V) - 1u;
-    const int64_t xw0 = xo0 - H, xl = xw0 + (int64_t)lane * V;
-    const int64_t yw0 = yo0 - HY;
-    const int64_t zi0 = zo0 - (int64_t)R * K;
-    const int nsteps = (int)(zo1 - zo0) + 2 * R * K;
+    // the first term of a plane (o_z = -R) in lexicographic order
+    constexpr int FOY = PAT == STENCIL_BOX ? -R : 0, FOX = PAT == STENCIL_BOX ? -R : 0;
+    const int l16 = lane & (F3_LX - 1);
+    const int row0 = (warp * 2 + (lane >> 4)) * RY;   // first own window row
+    const int xl = wsx + l16 * V;                     // first own column
+    const int zi0 = zo0 - R * K;
+    const int nsteps = (zo1 - zo0) + 2 * R * K;
     const int nsp = round_up_c(nsteps, U);
-    // column mask of this lane, row masks of this warp's rows (incl. halo)
+    // MASK: own columns inside the domain; x-neighbour columns outside it
+    bool keep[V], lout[R], rout[R];
     uint32_t cmask = 0;
 #pragma unroll
-    for (int v = 0; v < V; ++v)
-        if (xl + v >= 0 && xl + v < nx) cmask |= 1u << v;
-    const int row0 = warp * RY;                  // first own window row
-    // columns outside the domain: only warps that hold some need the selects
-    bool keep[V];
+    for (int v = 0; v < V; ++v) {
+        keep[v] = xl + v >= 0 && xl + v < nx;
+        cmask |= keep[v] ? 1u << v : 0u;
+    }
 #pragma unroll
-    for (int v = 0; v < V; ++v) keep[v] = (cmask >> v) & 1u;
+    for (int q = 0; q < R; ++q) {
+        lout[q] = xl - 1 - q < 0 || xl - 1 - q >= nx;
+        rout[q] = xl + V + q < 0 || xl + V + q >= nx;
+    }
     const bool need_cmask = MASK && __any_sync(0xffffffffu, cmask != FULLM);
-    const bool lane_out = (lane * V >= H) && (lane * V < H + BW);
 
     // ---- prologue: first stages
     if constexpr (PROD == PROD3_TMA) {
@@ -216,15 +301,14 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
             for (int q = 0; q < F3_STAGES && q < nsp; ++q) {
                 const uint32_t slot = (gst + q) % F3_STAGES;
                 mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
-                tma_load_3d(stages + (size_t)slot * G::PLANE, tmap, &bars[slot], (int)xw0, (int)yw0,
-                            (int)(zi0 + q));
+                tma_load_3d(stages + (size_t)slot * PLANE, tmap, &bars[slot], wsx, wsy, zi0 + q);
             }
         }
     } else {
         for (int q = 0; q < F3_STAGES - 1; ++q) {
             if (q < nsp)
-                plane_copy_async<DT>(stages + (size_t)((gst + q) % F3_STAGES) * G::PLANE, src, nx, ny, nz, !dir,
-                                     bval, xw0, yw0, zi0 + q, vec_ok);
+                plane_copy_async<DT, W, WY>(stages + (size_t)((gst + q) % F3_STAGES) * PLANE, src, nx, ny, nz, !dir,
+                                            bval, wsx, wsy, zi0 + q, vec_ok);
             cp_async_commit();
         }
     }
@@ -245,7 +329,7 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
         for (int ph = 0; ph < U; ++ph) {
             const int i = i0 + ph;
-            const int64_t zin = zi0 + i;
+            const int zin = zi0 + i;
             const uint32_t slot = (gst + i) % F3_STAGES;
             // ---- A: stage of plane zin ready
             if constexpr (PROD == PROD3_TMA) {
@@ -255,38 +339,27 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                 cp_async_wait<F3_STAGES - 2>();
                 __syncthreads();
                 if (i + F3_STAGES - 1 < nsp)
-                    plane_copy_async<DT>(stages + (size_t)((gst + i + F3_STAGES - 1) % F3_STAGES) * G::PLANE, src,
-                                         nx, ny, nz, !dir, bval, xw0, yw0, zin + F3_STAGES - 1, vec_ok);
+                    plane_copy_async<DT, W, WY>(stages + (size_t)((gst + i + F3_STAGES - 1) % F3_STAGES) * PLANE, src,
+                                                nx, ny, nz, !dir, bval, wsx, wsy, zin + F3_STAGES - 1, vec_ok);
                 cp_async_commit();
             }
             // ---- B: level-0 rows row0-R .. row0+RY-1+R of this plane
             C inc[NR][V];
             {
-                const S *pl = stages + (size_t)slot * G::PLANE;
+                const S *pl = stages + (size_t)slot * PLANE + l16 * V;
 #pragma unroll
                 for (int j = 0; j < NR; ++j) {
                     int wrow = row0 - R + j;
-                    wrow = wrow < 0 ? 0 : (wrow >= F3_WY ? F3_WY - 1 : wrow);   // beyond the window: halo garbage
-                    ldsvec<DT>(pl + wrow * W + lane * V, inc[j]);
+                    wrow = wrow < 0 ? 0 : (wrow >= WY ? WY - 1 : wrow);   // beyond the window: halo garbage
+                    ldsvec<DT>(pl + wrow * W, inc[j]);
                 }
                 if constexpr (MASK) {
-                    if ((uint32_t)zin >= (uint32_t)nz) {              // plane outside: uniform
+                    const bool zout = (unsigned)zin >= (unsigned)nz;
 #pragma unroll
-                        for (int j = 0; j < NR; ++j)
+                    for (int j = 0; j < NR; ++j) {
+                        const bool out = zout || (unsigned)(wsy + row0 - R + j) >= (unsigned)ny;
 #pragma unroll
-                            for (int v = 0; v < V; ++v) inc[j][v] = bval;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < NR; ++j) {
-                            const int y = (int)yw0 + row0 - R + j;    // warp-uniform
-                            if ((uint32_t)y >= (uint32_t)ny) {
-#pragma unroll
-                                for (int v = 0; v < V; ++v) inc[j][v] = bval;
-                            } else if (need_cmask) {
-#pragma unroll
-                                for (int v = 0; v < V; ++v) inc[j][v] = keep[v] ? inc[j][v] : bval;
-                            }
-                        }
+                        for (int v = 0; v < V; ++v) inc[j][v] = (out || (need_cmask && !keep[v])) ? bval : inc[j][v];
                     }
                 }
             }
@@ -297,149 +370,120 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                         fence_proxy_async_smem();
                         const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
                         mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
-                        tma_load_3d(stages + (size_t)sl2 * G::PLANE, tmap, &bars[sl2], (int)xw0, (int)yw0,
-                                    (int)(zi0 + i + F3_STAGES));
+                        tma_load_3d(stages + (size_t)sl2 * PLANE, tmap, &bars[sl2], wsx, wsy, zi0 + i + F3_STAGES);
                     }
                 }
             }
-            // ---- C: K levels
+            // ---- C: K levels.  inc: level-s rows of plane J = zin - sR.
 #pragma unroll
             for (int s = 0; s < K; ++s) {
+                const int s0 = ph % NS;   // slot of plane J - R (completed now), reused for J + R
                 C emit[RY][V];
-                // x-extended rows (star: only the own rows need x-neighbours)
-                C ext[NR][V + 2 * R];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    const bool need = (PAT == STENCIL_BOX) || (j >= R && j < R + RY);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) ext[j][R + v] = inc[j][v];
-                    if (need) {
-#pragma unroll
-                        for (int qq = 0; qq < R; ++qq) {
-                            ext[j][R - 1 - qq] = __shfl_up_sync(0xffffffffu, inc[j][V - 1 - qq], 1);
-                            ext[j][R + V + qq] = __shfl_down_sync(0xffffffffu, inc[j][qq], 1);
-                        }
-                    }
-                }
-                const int s0 = ph % NS;
-                // complete plane J - R: o_z = +R terms
 #pragma unroll
                 for (int j = 0; j < RY; ++j)
 #pragma unroll
                     for (int v = 0; v < V; ++v) emit[j][v] = P[s][s0][j][v];
+                // source rows in ascending order, so that each target row gets
+                // its terms in ascending (o_y, o_x) order within every o_z
 #pragma unroll
-                for (int oy = -R; oy <= R; ++oy)
+                for (int j = 0; j < NR; ++j) {
+                    const bool needx = PAT == STENCIL_BOX || (j >= R && j < R + RY);
+                    C ext[V + 2 * R];
+                    if (needx) {
+                        x_extend<C, V, R, MASK>(inc[j], ext, lout, rout, bval);
+                    } else {
 #pragma unroll
-                    for (int ox = -R; ox <= R; ++ox) {
-                        if (!Sh::inc(R, oy, ox)) continue;
-                        const C w = wr[Sh::widx(R, oy, ox)];
-#pragma unroll
-                        for (int j = 0; j < RY; ++j) row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], emit[j]);
+                        for (int v = 0; v < V; ++v) ext[R + v] = inc[j][v];
                     }
-                // planes J - R + m take their o_z = R - m terms
 #pragma unroll
-                for (int m = 1; m < NS; ++m) {
-                    const int oz = R - m, sl = (ph + m) % NS;
+                    for (int oy = -R; oy <= R; ++oy) {
+                        const int jt = j - R - oy;   // target row
+                        if (jt < 0 || jt >= RY) continue;
+                        // o_z = +R: the last terms of plane J - R
 #pragma unroll
-                    for (int oy = -R; oy <= R; ++oy)
+                        for (int ox = -R; ox <= R; ++ox)
+                            if (Sh::inc(R, oy, ox)) row_fma_s<C, V>(wr[Sh::widx(R, oy, ox)], &ext[R + ox], emit[jt]);
+                        // o_z = R - m: planes J - R + m (0 < m < 2R)
 #pragma unroll
-                        for (int ox = -R; ox <= R; ++ox) {
-                            if (!Sh::inc(oz, oy, ox)) continue;
-                            const C w = wr[Sh::widx(oz, oy, ox)];
+                        for (int m = 1; m < NS; ++m) {
+                            const int oz = R - m, sl = (ph + m) % NS;
 #pragma unroll
-                            for (int j = 0; j < RY; ++j) row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][sl][j]);
+                            for (int ox = -R; ox <= R; ++ox)
+                                if (Sh::inc(oz, oy, ox))
+                                    row_fma_s<C, V>(wr[Sh::widx(oz, oy, ox)], &ext[R + ox], P[s][sl][jt]);
                         }
-                }
-                // start plane J + R: o_z = -R terms, first one a multiply
-                {
-                    bool first = true;
-#pragma unroll
-                    for (int oy = -R; oy <= R; ++oy)
+                        // o_z = -R: the first terms of plane J + R (first one a multiply)
 #pragma unroll
                         for (int ox = -R; ox <= R; ++ox) {
                             if (!Sh::inc(-R, oy, ox)) continue;
-                            const C w = wr[Sh::widx(-R, oy, ox)];
-#pragma unroll
-                            for (int j = 0; j < RY; ++j) {
-                                if (first) row_mul_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][s0][j]);
-                                else row_fma_s<C, V>(w, &ext[j + R + oy][R + ox], P[s][s0][j]);
-                            }
-                            first = false;
+                            if (oy == FOY && ox == FOX) row_mul_s<C, V>(wr[Sh::widx(-R, oy, ox)], &ext[R + ox], P[s][s0][jt]);
+                            else row_fma_s<C, V>(wr[Sh::widx(-R, oy, ox)], &ext[R + ox], P[s][s0][jt]);
                         }
+                    }
                 }
-                // emitted plane index: Dirichlet cells keep the boundary value
-                const int ze = (int)zin - (s + 1) * R;
+                // emitted plane ze = J - R: Dirichlet cells keep the boundary value
+                const int ze = zin - (s + 1) * R;
                 if constexpr (MASK) {
-                    if ((uint32_t)ze >= (uint32_t)nz) {                // plane outside: uniform
+                    const bool zout = (unsigned)ze >= (unsigned)nz;
 #pragma unroll
-                        for (int j = 0; j < RY; ++j)
+                    for (int j = 0; j < RY; ++j) {
+                        const bool out = zout || (unsigned)(wsy + row0 + j) >= (unsigned)ny;
 #pragma unroll
-                            for (int v = 0; v < V; ++v) emit[j][v] = bval;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < RY; ++j) {
-                            const int y = (int)yw0 + row0 + j;         // warp-uniform
-                            if ((uint32_t)y >= (uint32_t)ny) {
-#pragma unroll
-                                for (int v = 0; v < V; ++v) emit[j][v] = bval;
-                            } else if (need_cmask) {
-#pragma unroll
-                                for (int v = 0; v < V; ++v) emit[j][v] = keep[v] ? emit[j][v] : bval;
-                            }
-                        }
+                        for (int v = 0; v < V; ++v)
+                            emit[j][v] = (out || (need_cmask && !keep[v])) ? bval : emit[j][v];
                     }
                 }
                 if (s + 1 < K) {
-                    // exchange the r edge rows with the warps above and below
-                    C *xb = xbuf + (size_t)xpar * F3_NWY * G::XROWS * W;
+                    // publish the emitted rows; read the r rows above and below
+                    C *xb = xbuf + (size_t)xpar * PLANE + l16 * V;
 #pragma unroll
-                    for (int qq = 0; qq < R; ++qq) {
-                        st_shared_vec<C, V>(xb + ((size_t)warp * G::XROWS + qq) * W + lane * V, emit[qq]);
-                        st_shared_vec<C, V>(xb + ((size_t)warp * G::XROWS + R + qq) * W + lane * V, emit[RY - R + qq]);
-                    }
+                    for (int j = 0; j < RY; ++j) st_shared_vec<C, V>(xb + (row0 + j) * W, emit[j]);
                     __syncthreads();
                     if (s == 0 && PROD == PROD3_TMA && threadIdx.x == 0 && i + F3_STAGES < nsp) {
                         // every warp has read this plane's stage: refill it
                         fence_proxy_async_smem();
                         const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
                         mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
-                        tma_load_3d(stages + (size_t)sl2 * G::PLANE, tmap, &bars[sl2], (int)xw0, (int)yw0,
-                                    (int)(zi0 + i + F3_STAGES));
+                        tma_load_3d(stages + (size_t)sl2 * PLANE, tmap, &bars[sl2], wsx, wsy, zi0 + i + F3_STAGES);
                     }
-                    const int wa = warp > 0 ? warp - 1 : warp;
-                    const int wb = warp + 1 < F3_NWY ? warp + 1 : warp;
 #pragma unroll
-                    for (int qq = 0; qq < R; ++qq) {
-                        ld_shared_vec<C, V>(xb + ((size_t)wa * G::XROWS + R + qq) * W + lane * V, inc[qq]);
-                        ld_shared_vec<C, V>(xb + ((size_t)wb * G::XROWS + qq) * W + lane * V, inc[R + RY + qq]);
+                    for (int j = 0; j < R; ++j) {
+                        const int ra = row0 - R + j, rb = row0 + RY + j;
+                        ld_shared_vec<C, V>(xb + (ra < 0 ? 0 : ra) * W, inc[j]);
+                        ld_shared_vec<C, V>(xb + (rb >= WY ? WY - 1 : rb) * W, inc[R + RY + j]);
+                        if constexpr (MASK) {
+                            // rows beyond the window that lie outside the domain
+                            const bool oa = (unsigned)(wsy + ra) >= (unsigned)ny || (unsigned)ze >= (unsigned)nz;
+                            const bool ob = (unsigned)(wsy + rb) >= (unsigned)ny || (unsigned)ze >= (unsigned)nz;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                inc[j][v] = oa ? bval : inc[j][v];
+                                inc[R + RY + j][v] = ob ? bval : inc[R + RY + j][v];
+                            }
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < RY; ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v) inc[R + j][v] = emit[j][v];
                     xpar ^= 1;
-                } else {
-                    // level K: store this warp's rows of the output tile
-                    if (ze >= zo0 && ze < zo1 && lane_out) {
+                } else if (ze >= zo0 && ze < zo1) {
+                    // level K: store this half-warp's rows of the output tile
 #pragma unroll
-                        for (int j = 0; j < RY; ++j) {
-                            const int wrow = row0 + j;
-                            const int64_t y = yw0 + wrow;
-                            if (wrow >= HY && wrow < HY + BY && y < ny) {
-                                S *rowp = dst + (ze * ny + y) * nx;
-                                if (vec_ok && xl + V <= nx) {
-                                    stvec<DT>(rowp + xl, emit[j]);
-                                } else {
+                    for (int j = 0; j < RY; ++j) {
+                        const int y = wsy + row0 + j;
+                        if (y < osy || y >= oey) continue;
+                        S *rowp = dst + ((int64_t)ze * ny + y) * nx;
+                        if (vec_ok && xl >= osx && xl + V <= oex) {
+                            stvec<DT>(rowp + xl, emit[j]);
+                        } else {
 #pragma unroll
-                                    for (int v = 0; v < V; ++v)
-                                        if (xl + v < nx) rowp[xl + v] = from_c<S>(emit[j][v]);
-                                }
-                            }
+                            for (int v = 0; v < V; ++v)
+                                if (xl + v >= osx && xl + v < oex) rowp[xl + v] = from_c<S>(emit[j][v]);
                         }
                     }
                 }
             }
-
         }
         if (bad) break;
     }
@@ -462,19 +506,25 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
     return true;
 }
 
-template <int DT, int R, int PAT, int K, int PROD>
+// A job of a Dirichlet grid whose window and z range stay strictly inside the
+// domain never meets a boundary cell or neighbour: it runs without masking.
+template <int W, int WY, int RK>
+__device__ __forceinline__ bool f3_interior(bool dir, int nx, int ny, int nz, int wsx, int wsy, int zo0, int zo1) {
+    return !dir || (wsx > 0 && wsx + W < nx && wsy > 0 && wsy + WY < ny && zo0 - RK >= 0 && zo1 + RK <= nz);
+}
+
+template <int DT, int R, int PAT, int K, int RY, int PROD>
 __global__ void __launch_bounds__(F3_THREADS, 1)
     fused3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F3Params<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    using G = F3Geo<DT, R, K>;
-    using Sh = Shape<3, R, PAT>;
+    using G = F3Geo<DT, R, K, RY>;
     extern __shared__ __align__(128) unsigned char smem[];
     S *stages = reinterpret_cast<S *>(smem);
     C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::STAGE_BYTES);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::STAGE_BYTES + G::XBUF_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nx = p.g.n2, ny = p.g.n1, nz = p.g.n0;
+    const int nx = (int)p.g.n2, ny = (int)p.g.n1, nz = (int)p.g.n0;
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
     if constexpr (PROD == PROD3_TMA) {
         if (threadIdx.x == 0) {
@@ -484,37 +534,38 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
         }
     }
     __syncthreads();
-    C wr[Sh::npts];
-#pragma unroll
-    for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
-    uint32_t gst = 0;   // planes consumed so far by this CTA (stage ring position)
-    int xpar = 0;       // exchange-buffer parity
+    const C *wr = p.w;   // parameter space: the FMAs read the weights as constant operands
+    uint32_t gst = 0;    // planes consumed so far by this CTA (stage ring position)
+    int xpar = 0;        // exchange-plane parity
     __shared__ unsigned long long s_ticket;
+    const int txy = p.ax.T * p.ay.T;
     // jobs are taken dynamically (faster SMs take more); the first and last z
     // ranges (Dirichlet edges) come first
-    const int64_t nch = p.jobs / (p.tiles_x * p.tiles_y);
     for (;;) {
         if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctl->ticket, 1ull);
         __syncthreads();
         const unsigned long long t = s_ticket;
         __syncthreads();
         if (t >= (unsigned long long)p.jobs) break;
-        const int64_t job = (int64_t)t;
-        const int64_t tx = job % p.tiles_x, rest = job / p.tiles_x;
-        const int64_t ty = rest % p.tiles_y, tc = rest / p.tiles_y;
-        const int64_t cz = nch < 2 ? tc : (tc == 0 ? 0 : tc == 1 ? nch - 1 : tc - 1);
-        const int64_t xo0 = tx * G::BW, yo0 = ty * G::BY;
-        const int64_t zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
-        // windows inside the domain never meet a Dirichlet cell: no masking code
-        const bool interior = !dir || (xo0 - G::H >= 0 && xo0 - G::H + G::W <= nx && yo0 - G::HY >= 0 &&
-                                       yo0 - G::HY + F3_WY <= ny && zo0 - R * K >= 0 && zo1 + R * K <= nz);
-        const bool ok = interior
-            ? fused3d_job<DT, R, PAT, K, PROD, false>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), nx,
-                                                     ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1, p.vec_ok != 0,
-                                                     stages, xbuf, bars, gst, xpar, lane, warp)
-            : fused3d_job<DT, R, PAT, K, PROD, true>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), nx,
-                                                    ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1, p.vec_ok != 0,
-                                                    stages, xbuf, bars, gst, xpar, lane, warp);
+        const int job = (int)t;
+        const int tx = job % p.ax.T, rest = job / p.ax.T;
+        const int ty = rest % p.ay.T, tc = rest / p.ay.T;
+        const int nch = p.chunks;
+        const int cz = nch < 2 ? tc : (tc == 0 ? 0 : tc == 1 ? nch - 1 : tc - 1);
+        int osx, oex, wsx, osy, oey, wsy;
+        f3_tile(p.ax, tx, osx, oex, wsx);
+        f3_tile(p.ay, ty, osy, oey, wsy);
+        const int zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
+        (void)txy;
+        const bool ok = f3_interior<G::W, G::WY, R * K>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
+            ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+                                                          nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
+                                                          zo0, zo1, p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane,
+                                                          warp)
+            : fused3d_job<DT, R, PAT, K, RY, PROD, true>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+                                                         nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
+                                                         zo0, zo1, p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane,
+                                                         warp);
         if (!ok) {
             if (threadIdx.x == 0) record_status(p.status, kStatusTimeout);
             break;
@@ -530,19 +581,20 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
 // All `passes` passes of K steps in one persistent launch (3D form of
 // fused2d_mp_kernel): CTAs take (pass, tile) items from one ticket,
 // pass-major and z-major within a pass; an item of pass p first waits until
-// every tile whose output meets its input window (up to 3 x 3 x 3 tiles, one
-// thread each) has finished pass p - 1; completion is published with release
-// semantics after the CTA's stores.  Waits are bounded (about one second); a
-// wait that gives up raises the abort flag and records STENCIL_ERR_TIMEOUT.
-template <int DT, int R, int PAT, int K, int PROD>
+// every tile whose output meets the dependency cone of its own output (its
+// output extended by rK on every axis, wrapped on periodic axes; up to
+// 3 x 3 x 3 tiles, one thread each) has finished pass p - 1; completion is
+// published with release semantics after the CTA's stores.  Waits are bounded
+// (about one second); a wait that gives up raises the abort flag and records
+// STENCIL_ERR_TIMEOUT.
+template <int DT, int R, int PAT, int K, int RY, int PROD>
 __global__ void __launch_bounds__(F3_THREADS, 1)
     fused3d_mp_kernel(const __grid_constant__ CUtensorMap tm_src0, const __grid_constant__ CUtensorMap tm_even,
                       const __grid_constant__ CUtensorMap tm_odd,
                       const __grid_constant__ F3MpParams<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    using G = F3Geo<DT, R, K>;
-    using Sh = Shape<3, R, PAT>;
+    using G = F3Geo<DT, R, K, RY>;
     extern __shared__ __align__(128) unsigned char smem[];
     S *stages = reinterpret_cast<S *>(smem);
     C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::STAGE_BYTES);
@@ -562,14 +614,13 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     __syncthreads();
     MpCtl *ctl = p.ctl;
     int *done = p.done;
-    C wr[Sh::npts];
-#pragma unroll
-    for (int j = 0; j < Sh::npts; ++j) wr[j] = p.w[j];
+    const C *wr = p.w;
     uint32_t gst = 0;
     int xpar = 0;
-    const int txy = p.tiles_x * p.tiles_y;
+    const int txy = p.ax.T * p.ay.T;
     const int jobs = txy * p.chunks;
     const unsigned long long items = (unsigned long long)jobs * (unsigned)p.passes;
+    constexpr int RK = R * K;
     __shared__ unsigned long long s_ticket;
     __shared__ int s_abort;
     // the next ticket and the abort flag are fetched one job ahead
@@ -592,20 +643,20 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
         }
         const int pass = (int)(t / (unsigned)jobs), j = (int)(t % (unsigned)jobs);
         const int cz = j / txy, rest = j - cz * txy;
-        const int ty = rest / p.tiles_x, tx = rest - ty * p.tiles_x;
-        const int xo0 = tx * G::BW, yo0 = ty * G::BY;
+        const int ty = rest / p.ax.T, tx = rest - ty * p.ax.T;
+        int osx, oex, wsx, osy, oey, wsy;
+        f3_tile(p.ax, tx, osx, oex, wsx);
+        f3_tile(p.ay, ty, osy, oey, wsy);
         const int zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
         if (pass > 0) {
-            const int xe = xo0 + G::BW < nx ? xo0 + G::BW : nx;
-            const int ye = yo0 + G::BY < ny ? yo0 + G::BY : ny;
-            const TileSpan sx = tile_span(xo0 - G::H, xe + G::H, nx, G::BW, !dir);
-            const TileSpan sy = tile_span(yo0 - G::HY, ye + G::HY, ny, G::BY, !dir);
-            const TileSpan sz = tile_span(zo0 - R * K, zo1 + R * K, nz, p.Lz, !dir);
+            const TileSpan sx = f3_span(p.ax, osx - RK, oex + RK, !dir);
+            const TileSpan sy = f3_span(p.ay, osy - RK, oey + RK, !dir);
+            const TileSpan sz = tile_span(zo0 - RK, zo1 + RK, nz, p.Lz, !dir);
             const int cx = sx.count(), cxy = cx * sy.count(), nd = cxy * sz.count();
             bool ok = true;
             for (int e = threadIdx.x; e < nd; e += F3_THREADS) {
                 const int ex = sx.at(e % cx), ey = sy.at((e % cxy) / cx), ez = sz.at(e / cxy);
-                ok = ok && wait_counter(&done[(ez * p.tiles_y + ey) * p.tiles_x + ex], pass, &ctl->abort);
+                ok = ok && wait_counter(&done[(ez * p.ay.T + ey) * p.ax.T + ex], pass, &ctl->abort);
             }
             // the barrier orders every thread's acquire before every thread's reads
             if (!__syncthreads_and(ok)) {
@@ -623,13 +674,13 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
         const S *src = static_cast<const S *>(pass == 0 ? p.src0 : from_even ? p.dst_even : p.dst_odd);
         const CUtensorMap *tm = pass == 0 ? &tm_src0 : from_even ? &tm_even : &tm_odd;
         S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
-        const bool interior = !dir || (xo0 - G::H >= 0 && xo0 - G::H + G::W <= nx && yo0 - G::HY >= 0 &&
-                                       yo0 - G::HY + F3_WY <= ny && zo0 - R * K >= 0 && zo1 + R * K <= nz);
-        const bool ok = interior
-            ? fused3d_job<DT, R, PAT, K, PROD, false>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1,
-                                                     p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane, warp)
-            : fused3d_job<DT, R, PAT, K, PROD, true>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, xo0, yo0, zo0, zo1,
-                                                    p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane, warp);
+        const bool ok = f3_interior<G::W, G::WY, RK>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
+            ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
+                                                          wsy, osy, oey, zo0, zo1, p.vec_ok != 0, stages, xbuf, bars,
+                                                          gst, xpar, lane, warp)
+            : fused3d_job<DT, R, PAT, K, RY, PROD, true>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
+                                                         wsy, osy, oey, zo0, zo1, p.vec_ok != 0, stages, xbuf, bars,
+                                                         gst, xpar, lane, warp);
         if (!ok) {
             if (threadIdx.x == 0) {
                 atomicExch(&ctl->abort, 1);
@@ -671,36 +722,49 @@ inline int64_t f3_lz(int64_t nz, int64_t tiles, int64_t slots, int rk, int lz) {
     return (nz + best_c - 1) / best_c;
 }
 
-template <int DT, int R, int PAT, int K>
-cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
-    using S = typename Traits<DT>::S;
-    using C = typename Traits<DT>::C;
-    using G = F3Geo<DT, R, K>;
-    F3Params<C> p;
+// Rows per half-warp: 2, or 1 where 2r k rows of y-halo would leave too
+// little of a 64-row window (and the partial planes too many registers).
+template <int DT, int R, int K> constexpr int f3_ry() { return R * K <= 4 ? 2 : 1; }
+
+template <typename Prm>
+void f3_fill_common(const stencil_plan_s &P, Prm &p, int W, int H, int WY, int HY) {
+    using C = std::remove_reference_t<decltype(p.w[0])>;
     p.g.n0 = P.n[0];
     p.g.n1 = P.n[1];
     p.g.n2 = P.n[2];
     p.g.bkind = P.bkind;
     p.g.bval = conv_w<C>(P.bval);
+    p.status = P.d_status;
+    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
+    const bool dir = P.bkind == STENCIL_DIRICHLET;
+    p.ax = f3_axis(P.n[2], W, H, dir);
+    p.ay = f3_axis(P.n[1], WY, HY, dir);
+}
+
+template <int DT, int R, int PAT, int K>
+cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    constexpr int RY = f3_ry<DT, R, K>();
+    using G = F3Geo<DT, R, K, RY>;
+    F3Params<C> p;
+    f3_fill_common(P, p, G::W, G::H, G::WY, G::HY);
     p.src = src;
     p.dst = dst;
-    p.status = P.d_status;
     p.ctl = static_cast<JobCtl *>(P.d_ctr);
-    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
     p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
-    bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && ((uintptr_t)src % 16 == 0) &&
-               nx < (1ll << 31) && ny < (1ll << 31) && nz < (1ll << 31);
+    bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && ((uintptr_t)src % 16 == 0);
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     if (tma) {
         const int64_t dims[3] = {nx, ny, nz};
-        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)F3_WY, 1u};
+        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)G::WY, 1u};
         tma = make_tmap(&map, DT, 3, dims, box, src);
     }
     // cp.async path: 16-byte copies need 16-byte aligned rows
     if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
-    auto kern = tma ? fused3d_kernel<DT, R, PAT, K, PROD3_TMA> : fused3d_kernel<DT, R, PAT, K, PROD3_CPASYNC>;
+    auto kern = tma ? fused3d_kernel<DT, R, PAT, K, RY, PROD3_TMA> : fused3d_kernel<DT, R, PAT, K, RY, PROD3_CPASYNC>;
     const int smem = G::SMEM;
     static bool attr_done[2] = {false, false};
     if (!attr_done[tma ? 0 : 1]) {
@@ -712,15 +776,13 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F3_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    p.tiles_x = (nx + G::BW - 1) / G::BW;
-    p.tiles_y = (ny + G::BY - 1) / G::BY;
-    const int64_t tiles = p.tiles_x * p.tiles_y;
+    const int64_t tiles = (int64_t)p.ax.T * p.ay.T;
     const int64_t slots = (int64_t)P.sm_count * bps;
     // z ranges: about three jobs per resident CTA (taken dynamically)
-    p.Lz = f3_lz(nz, tiles, slots, R * K, P.tile_rows);
-    const int64_t chunks = (nz + p.Lz - 1) / p.Lz;
-    p.jobs = tiles * chunks;
-    int64_t grid = p.jobs < slots ? p.jobs : slots;
+    p.Lz = (int)f3_lz(nz, tiles, slots, R * K, P.tile_rows);
+    p.chunks = (int)((nz + p.Lz - 1) / p.Lz);
+    p.jobs = tiles * p.chunks;
+    const int64_t grid = p.jobs < slots ? p.jobs : slots;
     kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(map, p);
     return cudaGetLastError();
 }
@@ -730,20 +792,15 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
                           cudaStream_t st) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    using G = F3Geo<DT, R, K>;
+    constexpr int RY = f3_ry<DT, R, K>();
+    using G = F3Geo<DT, R, K, RY>;
     if (!fused3d_multi_ok(P, K) || passes < 1) return cudaErrorNotSupported;
     F3MpParams<C> p;
-    p.g.n0 = P.n[0];
-    p.g.n1 = P.n[1];
-    p.g.n2 = P.n[2];
-    p.g.bkind = P.bkind;
-    p.g.bval = conv_w<C>(P.bval);
+    f3_fill_common(P, p, G::W, G::H, G::WY, G::HY);
     p.src0 = src0;
     p.dst_even = dst_even;
     p.dst_odd = dst_odd;
     p.passes = passes;
-    p.status = P.d_status;
-    for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
     const bool al = ((uintptr_t)src0 % 16 == 0) && ((uintptr_t)dst_even % 16 == 0) && ((uintptr_t)dst_odd % 16 == 0);
     p.vec_ok = (nx % G::V == 0) && al;
@@ -752,12 +809,13 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     memset(maps, 0, sizeof(maps));
     if (tma) {
         const int64_t dims[3] = {nx, ny, nz};
-        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)F3_WY, 1u};
+        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)G::WY, 1u};
         const void *bases[3] = {src0, dst_even, dst_odd};
         for (int i = 0; i < 3 && tma; ++i) tma = make_tmap(&maps[i], DT, 3, dims, box, bases[i]);
     }
     if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
-    auto kern = tma ? fused3d_mp_kernel<DT, R, PAT, K, PROD3_TMA> : fused3d_mp_kernel<DT, R, PAT, K, PROD3_CPASYNC>;
+    auto kern = tma ? fused3d_mp_kernel<DT, R, PAT, K, RY, PROD3_TMA>
+                    : fused3d_mp_kernel<DT, R, PAT, K, RY, PROD3_CPASYNC>;
     const int smem = G::SMEM;
     static bool attr_done[2] = {false, false};
     if (!attr_done[tma ? 0 : 1]) {
@@ -769,14 +827,12 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F3_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    const int64_t tiles_x = (nx + G::BW - 1) / G::BW, tiles_y = (ny + G::BY - 1) / G::BY;
+    const int64_t txy = (int64_t)p.ax.T * p.ay.T;
     const int64_t slots = (int64_t)P.sm_count * bps;
-    const int64_t lz = f3_lz(nz, tiles_x * tiles_y, slots, R * K, P.tile_rows);
+    const int64_t lz = f3_lz(nz, txy, slots, R * K, P.tile_rows);
     const int64_t chunks = (nz + lz - 1) / lz;
-    const int64_t tiles = tiles_x * tiles_y * chunks;
-    if (tiles >= (1ll << 28)) return cudaErrorNotSupported;
-    p.tiles_x = (int)tiles_x;
-    p.tiles_y = (int)tiles_y;
+    const int64_t tiles = txy * chunks;
+    if (tiles >= (1ll << 28) || tiles * passes >= (1ll << 62)) return cudaErrorNotSupported;
     p.chunks = (int)chunks;
     p.Lz = (int)lz;
     p.tiles = (int)tiles;
@@ -790,49 +846,66 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     return cudaGetLastError();
 }
 
-template <int DT> constexpr int f3_kmax(int r) { return r == 1 ? 4 : 2; }
+// Largest K instantiated for (dtype, r): bounded by the registers that hold
+// 2r partial planes per level (128 per thread at 512 threads).
+template <int DT> constexpr int f3_kmax(int r, int pat) {
+    return r == 1 ? 4 : (r == 2 && pat == STENCIL_STAR) ? 2 : 1;
+}
 
 template <int DT, int R, int PAT>
 cudaError_t launch_f3mp_k(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
                           cudaStream_t st) {
+    constexpr int KM = f3_kmax<DT>(R, PAT);
     switch (k) {
         case 1: return launch_f3mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st);
-        case 2: return launch_f3mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st);
-        case 3: if constexpr (R == 1) return launch_f3mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
-        case 4: if constexpr (R == 1) return launch_f3mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
+        case 2: if constexpr (KM >= 2) return launch_f3mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st); break;
+        case 3: if constexpr (KM >= 3) return launch_f3mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
+        case 4: if constexpr (KM >= 4) return launch_f3mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
     }
     return cudaErrorInvalidValue;
+}
+
+// one radius, both patterns (radius 1 in k_fused3d_mp_<dtype>.cu, radii 2 and
+// 3 in k_fused3d_mp_<dtype>_r23.cu: the build compiles them in parallel)
+template <int DT, int R>
+cudaError_t launch_f3mp_r(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
+                          cudaStream_t st) {
+    return P.pattern == STENCIL_BOX ? launch_f3mp_k<DT, R, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
+                                    : launch_f3mp_k<DT, R, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
 }
 
 template <int DT>
 cudaError_t launch_f3mp_dt(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
                            cudaStream_t st) {
-    const bool box = P.pattern == STENCIL_BOX;
-    if (P.r == 1) return box ? launch_f3mp_k<DT, 1, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
-                             : launch_f3mp_k<DT, 1, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
-    if (P.r == 2) return box ? launch_f3mp_k<DT, 2, STENCIL_BOX>(P, src0, de, dof, k, passes, st)
-                             : launch_f3mp_k<DT, 2, STENCIL_STAR>(P, src0, de, dof, k, passes, st);
+    if (P.r == 1) return launch_f3mp_r<DT, 1>(P, src0, de, dof, k, passes, st);
+    if (P.r == 2) return launch_f3mp_r<DT, 2>(P, src0, de, dof, k, passes, st);
+    if (P.r == 3) return launch_f3mp_r<DT, 3>(P, src0, de, dof, k, passes, st);
     return cudaErrorInvalidValue;
 }
 
 template <int DT, int R, int PAT>
 cudaError_t launch_f3_k(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    constexpr int KM = f3_kmax<DT>(R, PAT);
     switch (k) {
         case 1: return launch_f3_t<DT, R, PAT, 1>(P, src, dst, st);
-        case 2: return launch_f3_t<DT, R, PAT, 2>(P, src, dst, st);
-        case 3: if constexpr (R == 1) return launch_f3_t<DT, R, PAT, 3>(P, src, dst, st); break;
-        case 4: if constexpr (R == 1) return launch_f3_t<DT, R, PAT, 4>(P, src, dst, st); break;
+        case 2: if constexpr (KM >= 2) return launch_f3_t<DT, R, PAT, 2>(P, src, dst, st); break;
+        case 3: if constexpr (KM >= 3) return launch_f3_t<DT, R, PAT, 3>(P, src, dst, st); break;
+        case 4: if constexpr (KM >= 4) return launch_f3_t<DT, R, PAT, 4>(P, src, dst, st); break;
     }
     return cudaErrorInvalidValue;
 }
 
+template <int DT, int R>
+cudaError_t launch_f3_r(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
+    return P.pattern == STENCIL_BOX ? launch_f3_k<DT, R, STENCIL_BOX>(P, src, dst, k, st)
+                                    : launch_f3_k<DT, R, STENCIL_STAR>(P, src, dst, k, st);
+}
+
 template <int DT>
 cudaError_t launch_f3_dt(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
-    const bool box = P.pattern == STENCIL_BOX;
-    if (P.r == 1) return box ? launch_f3_k<DT, 1, STENCIL_BOX>(P, src, dst, k, st)
-                             : launch_f3_k<DT, 1, STENCIL_STAR>(P, src, dst, k, st);
-    if (P.r == 2) return box ? launch_f3_k<DT, 2, STENCIL_BOX>(P, src, dst, k, st)
-                             : launch_f3_k<DT, 2, STENCIL_STAR>(P, src, dst, k, st);
+    if (P.r == 1) return launch_f3_r<DT, 1>(P, src, dst, k, st);
+    if (P.r == 2) return launch_f3_r<DT, 2>(P, src, dst, k, st);
+    if (P.r == 3) return launch_f3_r<DT, 3>(P, src, dst, k, st);
     return cudaErrorInvalidValue;
 }
 

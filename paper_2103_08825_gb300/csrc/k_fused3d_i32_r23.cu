@@ -1,0 +1,8 @@
+// k_fused3d_i32_r23.cu -- the 3D fused kernel for STENCIL_I32 storage, radii 2
+// and 3 (own translation unit: the build compiles in parallel).
+#include "k_fused3d.cuh"
+
+namespace sg {
+template cudaError_t launch_f3_r<STENCIL_I32, 2>(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+template cudaError_t launch_f3_r<STENCIL_I32, 3>(const stencil_plan_s &, const void *, void *, int, cudaStream_t);
+}  // namespace sg

@@ -1,8 +1,12 @@
-// k_fused3d_mp_f16.cu -- instantiations of the persistent multi-pass 3D kernel for
-// STENCIL_F16 storage (own translation unit: the build compiles in parallel).
+// k_fused3d_mp_f16.cu -- the persistent multi-pass 3D kernel for STENCIL_F16
+// storage, radius 1, and its dispatcher (radii 2 and 3: k_fused3d_mp_f16_r23.cu).
 #include "k_fused3d.cuh"
 
 namespace sg {
+extern template cudaError_t launch_f3mp_r<STENCIL_F16, 2>(const stencil_plan_s &, const void *, void *, void *, int,
+                                                           int, cudaStream_t);
+extern template cudaError_t launch_f3mp_r<STENCIL_F16, 3>(const stencil_plan_s &, const void *, void *, void *, int,
+                                                           int, cudaStream_t);
 cudaError_t launch_f3mp_F16(const stencil_plan_s &P, const void *src0, void *de, void *dof, int k, int passes,
                             cudaStream_t st) {
     return launch_f3mp_dt<STENCIL_F16>(P, src0, de, dof, k, passes, st);

@@ -27,12 +27,18 @@ struct stencil_plan_s {
     int eval_to_compact[sg::kHostMaxPts] = {};
     int k = 0;                 // 0 = default
     int tile_rows = 0;         // 2D fused tile height (0 = default)
+    int block_warps = 0;       // 2D fused kernels: warps per CTA (0 = default 4)
     int variant = STENCIL_VARIANT_FUSED;
     bool tuned_plain = false;  // the tuner found the one-step kernel fastest
     int device = 0;
     int sm_count = 0;
     void *ws = nullptr;        // one grid: intermediate passes of stencil_run
     void *hws[2] = {nullptr, nullptr};   // device copies for stencil_run_host
+    // stencil_run_host_many: two input and two output grids, copy streams, events
+    void *hm_buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t hm_st[2] = {nullptr, nullptr};
+    cudaEvent_t hm_ev[7] = {};
+    bool hm_ready = false;
     size_t grid_bytes = 0;
     int *d_status = nullptr;   // device status word (0 = OK)
     void *d_ctr = nullptr;     // job tickets of the per-pass kernels (sg::JobCtl, same allocation)
@@ -40,7 +46,12 @@ struct stencil_plan_s {
     // per tile; every launch leaves them at zero
     mutable void *d_mp = nullptr;
     mutable int64_t mp_tiles_cap = 0;
-    // adjoint workspace
+    // in-place sweep: two ring buffers
+    void *inpl_ws = nullptr;
+    size_t inpl_ws_bytes = 0;
+    // adjoint: plan-owned checkpoints (stencil_adjoint_run) and workspace
+    void *ckpt_ws = nullptr;
+    size_t ckpt_ws_bytes = 0;
     void *adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
     double *adj_partials = nullptr;
@@ -93,5 +104,10 @@ bool make_tmap(CUtensorMap *map, int dtype, int rank, const int64_t *dims_inner_
                const void *base);
 
 void set_error(const std::string &msg);
+stencil_status_t cuda_fail(cudaError_t e, const char *what);
+stencil_status_t ensure_buf(void **buf, size_t bytes);
+stencil_status_t ensure_status_word(stencil_plan_s *P);
+// T steps by tessellate tiling (k_tess.cu)
+stencil_status_t tess_run(stencil_plan_s *P, const void *u_in, void *u_out, int64_t T, cudaStream_t st);
 
 }  // namespace sg

@@ -167,3 +167,33 @@ def test_batch_full_workload():
     for x, y in zip(xs[:16], ys[:16]):
         m0, m1 = x.double().sum().item(), y.double().sum().item()
         assert abs(m1 - m0) <= 1e-4 * abs(m0)
+
+
+@pytest.mark.parametrize("bkind", [PERIODIC, DIRICHLET])
+def test_batch_config_and_tune_keep_results(bkind):
+    """Every fusion depth and tile height of the batch, and the tuner's
+    choice, give results bit-identical to per-grid stencil_run calls."""
+    sg = sgmod()
+    probs = random_batch(16, 90 + bkind, BOX, bkind)
+    xs = [torch.from_numpy(uniform01(p.seed, p.npts).reshape(p.shape).astype(np.float32)).to(DEV) for p in probs]
+    ref = single_runs(sg, probs, xs, sg.STENCIL_F32)
+    b = sg.stencil_batch_create([p.shape for p in probs], [p.weights for p in probs], [p.T for p in probs], BOX, 1,
+                                bkind, 0.0, sg.STENCIL_F32)
+    ys = [torch.empty_like(x) for x in xs]
+    for k in (1, 2, 3, 4):
+        for rows in (16, 32, 128):
+            if rows < 4 * k:
+                continue
+            sg.stencil_batch_set_config(b, k, rows)
+            assert sg.stencil_batch_get_config(b) == (k, rows)
+            sg.stencil_batch_run(b, xs, ys)
+            torch.cuda.synchronize()
+            assert sg.stencil_batch_get_device_status(b) == 0
+            for i, (y, r) in enumerate(zip(ys, ref)):
+                assert torch.equal(y, r), (k, rows, i)
+    ms = sg.stencil_batch_tune(b, xs, ys)
+    assert ms > 0
+    sg.stencil_batch_run(b, xs, ys)
+    torch.cuda.synchronize()
+    for y, r in zip(ys, ref):
+        assert torch.equal(y, r)

@@ -333,10 +333,15 @@ def sample_points_3d(shape, n_random=40, seed=7):
     rng = np.random.default_rng(seed)
     nz, ny, nx = shape
     pts = {(0, 0, 0), (nz - 1, ny - 1, nx - 1), (0, ny - 1, 0), (nz // 2, 0, nx - 1)}
-    for x in (119, 120, 239, 240, 111, 112):   # x seams of the fused 3D tiles
+    # seams of the fused 3D tiles: 64-wide windows with a 4-column halo in x
+    # (first tile 60 columns, then 56), 64-row windows with a k-row halo in y
+    # (first tile 64 - k rows, then 64 - 2k), for k = 1..4
+    for x in (59, 60, 115, 116, 171, 172, nx - 61, nx - 60):
         pts.add((int(rng.integers(0, nz)), int(rng.integers(0, ny)), x))
-    for y in (23, 24, 25, 27, 28, 29, 30, 31):   # y seams
-        pts.add((int(rng.integers(0, nz)), y, int(rng.integers(0, nx))))
+    for k in range(1, 5):
+        f, b = 64 - k, 64 - 2 * k
+        for y in (f - 1, f, f + b - 1, f + b, ny - f - 1, ny - f):
+            pts.add((int(rng.integers(0, nz)), y, int(rng.integers(0, nx))))
     for _ in range(n_random):
         pts.add(tuple(int(rng.integers(0, s)) for s in shape))
     return np.array(sorted(pts), dtype=np.int64)
