@@ -105,7 +105,10 @@ SG_DECL_F3(I32)
 // the 2r partial planes per level each thread keeps in registers.
 int fused3d_max_k(const stencil_plan_s &P) {
     if (P.dim != 3 || P.r > 3 || P.n[0] > (1ll << 30) || P.n[1] > (1ll << 30) || P.n[2] > (1ll << 30)) return 0;
-    return P.r == 1 ? 4 : (P.r == 2 && P.pattern == STENCIL_STAR) ? 2 : 1;
+    // the 125- and 343-point boxes have no fused form: one partial plane per
+    // level already fills the register file, so they run the plain sweep
+    if (P.pattern == STENCIL_BOX && P.r > 1) return 0;
+    return P.r == 1 ? 4 : P.r == 2 ? 2 : 1;
 }
 
 cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {

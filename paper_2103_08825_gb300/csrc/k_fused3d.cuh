@@ -7,9 +7,9 @@
 // Here a CTA owns an xy window of W x WY points and streams the planes of a z
 // range through it:
 //
-//   threads   16 warps; each half-warp (16 lanes x V contiguous values = W
-//             columns) owns RY consecutive rows of the window, so a warp holds
-//             2 RY rows and the CTA 32 RY;
+//   threads   each half-warp (16 lanes x V contiguous values = W columns)
+//             owns RY consecutive rows of the 64-row window, so a warp holds
+//             2 RY rows and the CTA 32 / RY warps (RY = 2 or 4);
 //   levels    every incoming plane of level s adds its terms to the 2r
 //             partial planes of level s+1 it touches (registers); the plane
 //             that receives its last term is emitted as level s+1's input;
@@ -18,7 +18,7 @@
 //             level s+1 rows from an exchange plane every half-warp writes
 //             its emitted rows into (one CTA barrier per level);
 //   input     PROD3_TMA: one thread loads whole window planes with 3D TMA
-//             into a 6-stage ring (mbarrier completion, bounded waits);
+//             into an 8-stage ring (mbarrier completion, bounded waits);
 //             PROD3_CPASYNC: every thread copies its share of the plane with
 //             cp.async, indices wrapped (periodic grids, unaligned rows);
 //   tiling    overlapped (the window recomputes an r k halo), but on a
@@ -41,10 +41,9 @@
 
 namespace sg {
 
-constexpr int F3_NW = 16;                // warps per CTA
-constexpr int F3_THREADS = F3_NW * 32;
+constexpr int F3_WY = 64;                // window rows: 32 / RY warps of two RY-row half-warps
 constexpr int F3_LX = 16;                // lanes along x: a half-warp spans the window's width
-constexpr int F3_STAGES = 6;             // plane ring depth (TMA)
+constexpr int F3_STAGES = 8;             // plane ring depth (a power of two: cheap ring indices)
 enum { PROD3_TMA = 0, PROD3_CPASYNC = 1 };
 
 template <int DT, int R, int K, int RY> struct F3Geo {
@@ -52,14 +51,22 @@ template <int DT, int R, int K, int RY> struct F3Geo {
     using C = typename Traits<DT>::C;
     static constexpr int V = Traits<DT>::V;
     static constexpr int W = F3_LX * V;                              // window columns
-    static constexpr int WY = 2 * F3_NW * RY;                        // window rows
+    static constexpr int WY = F3_WY;                                 // window rows
+    static constexpr int NW = F3_WY / (2 * RY);                      // warps per CTA
+    static constexpr int THREADS = NW * 32;
     static constexpr int AL = max_c(align_elems<DT>(), V);
     static constexpr int H = round_up_c(R * K, AL);                  // x halo of an interior tile
     static constexpr int HY = R * K;                                 // y halo
-    static constexpr int PLANE = W * WY;
-    static constexpr int STAGE_BYTES = PLANE * (int)sizeof(S);
-    static constexpr int XBUF_BYTES = 2 * PLANE * (int)sizeof(C);    // exchange plane, double-buffered
-    static constexpr int SMEM = F3_STAGES * STAGE_BYTES + XBUF_BYTES + F3_STAGES * 8;
+    // a stage slot or exchange plane holds the window's WY rows between R
+    // guard rows above and R below that keep the boundary value
+    static constexpr int WYG = WY + 2 * R;
+    static constexpr int SLOT = W * WYG;                             // elements
+    static constexpr int SLOT_BYTES = SLOT * (int)sizeof(S);
+    static constexpr int TMA_BYTES = W * WY * (int)sizeof(S);        // one window plane
+    static constexpr int XPLANE = SLOT;
+    static constexpr int XBUF_BYTES = 2 * XPLANE * (int)sizeof(C);   // exchange plane, double-buffered
+    static constexpr int SMEM = F3_STAGES * SLOT_BYTES + XBUF_BYTES + F3_STAGES * 8;
+    static_assert((R * W * (int)sizeof(S)) % 128 == 0 && SLOT_BYTES % 128 == 0, "TMA destination alignment");
     static_assert(W - 2 * H >= V && WY - 2 * HY >= 1, "fusion depth too large for the window");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -174,7 +181,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // thread copies the same 16-byte column chunk of several rows; a chunk that
 // lies outside a periodic grid is wrapped by one extent, and when the grid's
 // rows are 16-byte multiples it is still one aligned 16-byte copy.
-template <int DT, int W, int WY>
+template <int DT, int W, int WY, int THREADS>
 __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, const typename Traits<DT>::S *src,
                                                  int64_t nx, int64_t ny, int64_t nz, bool periodic,
                                                  typename Traits<DT>::C bval, int64_t xw0, int64_t yw0, int64_t z,
@@ -182,8 +189,8 @@ __device__ __forceinline__ void plane_copy_async(typename Traits<DT>::S *stage, 
     using S = typename Traits<DT>::S;
     constexpr int VE = 16 / (int)sizeof(S);   // elements per 16-byte copy
     constexpr int TPR = W / VE;               // threads per window row
-    constexpr int RSTEP = F3_THREADS / TPR;   // rows per sweep of the block
-    static_assert(W % VE == 0 && F3_THREADS % TPR == 0, "chunking");
+    constexpr int RSTEP = THREADS / TPR;      // rows per sweep of the block
+    static_assert(W % VE == 0 && THREADS % TPR == 0, "chunking");
     bool zin = z >= 0 && z < nz;
     if (!zin && periodic) { z = wrap_idx(z, nz); zin = true; }
     const int col = (int)(threadIdx.x % TPR) * VE;
@@ -251,48 +258,87 @@ __device__ __forceinline__ void x_extend(const C *x, C *ext, const bool *lout, c
     }
 }
 
+// Boundary value into the guard rows of every stage slot and both exchange
+// planes (rows that no copy and no exchange ever writes).  Once per launch,
+// before the CTA's first job; the caller's barrier publishes it.
+template <int DT, int R, int K, int RY>
+__device__ __forceinline__ void f3_guard_init(typename Traits<DT>::S *stages, typename Traits<DT>::C *xbuf,
+                                              typename Traits<DT>::C bval) {
+    using G = F3Geo<DT, R, K, RY>;
+    constexpr int W = G::W, GE = 2 * R * W;   // guard elements per slot
+    for (int e = threadIdx.x; e < (F3_STAGES + 2) * GE; e += G::THREADS) {
+        const int sl = e / GE, q = e - sl * GE;
+        const int row = q / W < R ? q / W : q / W + G::WY, col = q % W;
+        if (sl < F3_STAGES) stages[(size_t)sl * G::SLOT + row * W + col] = from_c<typename Traits<DT>::S>(bval);
+        else xbuf[(size_t)(sl - F3_STAGES) * G::XPLANE + row * W + col] = bval;
+    }
+}
+
 // One job: the output tile [osx, oex) x [osy, oey) x [zo0, zo1) from the
 // window columns [wsx, wsx + W) and rows [wsy, wsy + WY), streaming the planes
-// zo0 - rK .. zo1 + rK - 1.  MASK: the job reaches the Dirichlet boundary, so
-// cells and window-edge neighbours outside the domain take the boundary value
-// at every level.  Returns false if a bounded wait gave up.
+// zo0 - rK .. zo1 + rK - 1.
+//
+// Boundary handling (MASK: the job reaches the Dirichlet boundary).  Windows
+// never extend past the domain (boundary-aware tiling), so in the steady
+// state the only values from outside are (a) rows just beyond the window --
+// the slots' and exchange planes' guard rows, which hold the boundary value --
+// and (b) columns just beyond the window, which the window-edge lanes take
+// from the boundary value by a select after their shuffles.  Planes outside
+// the domain occur only in the first and last 2rK planes of the stream (the
+// TMA fills them with zeros, and the levels emit planes there); those
+// iterations, and every iteration of a window larger than the grid
+// (`small`), run a second instance of the loop body that resets every cell
+// outside the domain to the boundary value at every level.  Returns false if
+// a bounded wait gave up.
 template <int DT, int R, int PAT, int K, int RY, int PROD, bool MASK>
 __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typename Traits<DT>::S *__restrict__ src,
                                             typename Traits<DT>::S *__restrict__ dst, int nx, int ny, int nz,
                                             bool dir, typename Traits<DT>::C bval, const typename Traits<DT>::C *wr,
                                             int wsx, int osx, int oex, int wsy, int osy, int oey, int zo0, int zo1,
-                                            bool vec_ok, typename Traits<DT>::S *stages, typename Traits<DT>::C *xbuf,
-                                            uint64_t *bars, uint32_t &gst, int &xpar, int lane, int warp) {
+                                            bool vec_ok, bool small, typename Traits<DT>::S *stages,
+                                            typename Traits<DT>::C *xbuf, uint64_t *bars, uint32_t &gst, int lane,
+                                            int warp) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
     using G = F3Geo<DT, R, K, RY>;
     using Sh = Shape<3, R, PAT>;
-    constexpr int V = G::V, W = G::W, WY = G::WY, PLANE = G::PLANE;
+    constexpr int V = G::V, W = G::W, WY = G::WY, SLOT = G::SLOT;
     constexpr int NS = 2 * R, NR = RY + 2 * R;   // NR: rows a half-warp reads, with the y-halo
     constexpr int U = NS;                        // z unroll: partial-plane slots repeat every 2R
-    constexpr uint32_t FULLM = (1u << V) - 1u;
+    constexpr int RK = R * K;
     // the first term of a plane (o_z = -R) in lexicographic order
     constexpr int FOY = PAT == STENCIL_BOX ? -R : 0, FOX = PAT == STENCIL_BOX ? -R : 0;
     const int l16 = lane & (F3_LX - 1);
     const int row0 = (warp * 2 + (lane >> 4)) * RY;   // first own window row
     const int xl = wsx + l16 * V;                     // first own column
-    const int zi0 = zo0 - R * K;
-    const int nsteps = (zo1 - zo0) + 2 * R * K;
+    const int zi0 = zo0 - RK;
+    const int nsteps = (zo1 - zo0) + 2 * RK;
     const int nsp = round_up_c(nsteps, U);
-    // MASK: own columns inside the domain; x-neighbour columns outside it
-    bool keep[V], lout[R], rout[R];
-    uint32_t cmask = 0;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        keep[v] = xl + v >= 0 && xl + v < nx;
-        cmask |= keep[v] ? 1u << v : 0u;
-    }
+    // a thread's reads start at window row row0 - R = slot row row0
+    const int rdoff = row0 * W + l16 * V;
+    // neighbour columns outside the domain (window-edge lanes of an edge window)
+    bool lout[R], rout[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        lout[q] = xl - 1 - q < 0 || xl - 1 - q >= nx;
-        rout[q] = xl + V + q < 0 || xl + V + q >= nx;
+        lout[q] = MASK && (xl - 1 - q < 0 || xl - 1 - q >= nx);
+        rout[q] = MASK && (xl + V + q < 0 || xl + V + q >= nx);
     }
-    const bool need_cmask = MASK && __any_sync(0xffffffffu, cmask != FULLM);
+    // masked iterations: own columns and the NR rows read (bit j: window row
+    // row0 - R + j) outside the domain
+    bool keep[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) keep[v] = xl + v >= 0 && xl + v < nx;
+    uint32_t yout_bits = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) yout_bits |= (unsigned)(wsy + row0 - R + j) >= (unsigned)ny ? 1u << j : 0u;
+    // stores: rows of the output tile, whole vectors inside it
+    uint32_t ystore = 0;
+#pragma unroll
+    for (int j = 0; j < RY; ++j) ystore |= (wsy + row0 + j >= osy && wsy + row0 + j < oey) ? 1u << j : 0u;
+    const bool xvec = vec_ok && xl >= osx && xl + V <= oex;
+    const bool xsome = !xvec && xl + V > osx && xl < oex;   // part of the lane's columns
+    S *const orow = dst + (int64_t)(wsy + row0) * nx + xl;   // own first row, plane 0
+    const int64_t pstride = (int64_t)nx * ny;
 
     // ---- prologue: first stages
     if constexpr (PROD == PROD3_TMA) {
@@ -300,15 +346,15 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
             fence_proxy_async_smem();
             for (int q = 0; q < F3_STAGES && q < nsp; ++q) {
                 const uint32_t slot = (gst + q) % F3_STAGES;
-                mbar_arrive_expect_tx(&bars[slot], G::STAGE_BYTES);
-                tma_load_3d(stages + (size_t)slot * PLANE, tmap, &bars[slot], wsx, wsy, zi0 + q);
+                mbar_arrive_expect_tx(&bars[slot], G::TMA_BYTES);
+                tma_load_3d(stages + (size_t)slot * SLOT + R * W, tmap, &bars[slot], wsx, wsy, zi0 + q);
             }
         }
     } else {
         for (int q = 0; q < F3_STAGES - 1; ++q) {
             if (q < nsp)
-                plane_copy_async<DT, W, WY>(stages + (size_t)((gst + q) % F3_STAGES) * PLANE, src, nx, ny, nz, !dir,
-                                            bval, wsx, wsy, zi0 + q, vec_ok);
+                plane_copy_async<DT, W, WY, G::THREADS>(stages + (size_t)((gst + q) % F3_STAGES) * SLOT + R * W, src, nx, ny, nz,
+                                            !dir, bval, wsx, wsy, zi0 + q, vec_ok);
             cp_async_commit();
         }
     }
@@ -323,54 +369,59 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
 #pragma unroll
                 for (int v = 0; v < V; ++v) P[s][m][j][v] = C(0);
 
+    // A bounded wait that gives up is voted on at the level's first CTA
+    // barrier; from then on the job only runs out its loop (no waits, copies
+    // or stores) and returns false.
     bool bad = false;
     int ibad = 0;   // the plane whose stage a bounded wait gave up on
-    for (int i0 = 0; i0 < nsp; i0 += U) {
+
+    // One unrolled group of U planes; ZM: the masked instance.
+    auto group = [&](auto zm_tag, const int i0) {
+        constexpr bool ZM = decltype(zm_tag)::value;
 #pragma unroll
         for (int ph = 0; ph < U; ++ph) {
             const int i = i0 + ph;
             const int zin = zi0 + i;
-            const uint32_t slot = (gst + i) % F3_STAGES;
+            const uint32_t g = gst + (uint32_t)i, slot = g % F3_STAGES;
             // ---- A: stage of plane zin ready
+            bool waitbad = false;
             if constexpr (PROD == PROD3_TMA) {
-                const bool ok = mbar_wait_bounded(&bars[slot], ((gst + i) / F3_STAGES) & 1u);
-                if (__syncthreads_or(!ok)) { bad = true; ibad = i; break; }
+                if (!bad) waitbad = !mbar_wait_bounded(&bars[slot], (g / F3_STAGES) & 1u);
             } else {
                 cp_async_wait<F3_STAGES - 2>();
                 __syncthreads();
                 if (i + F3_STAGES - 1 < nsp)
-                    plane_copy_async<DT, W, WY>(stages + (size_t)((gst + i + F3_STAGES - 1) % F3_STAGES) * PLANE, src,
-                                                nx, ny, nz, !dir, bval, wsx, wsy, zin + F3_STAGES - 1, vec_ok);
+                    plane_copy_async<DT, W, WY, G::THREADS>(stages + (size_t)((g + F3_STAGES - 1) % F3_STAGES) * SLOT + R * W,
+                                                src, nx, ny, nz, !dir, bval, wsx, wsy, zin + F3_STAGES - 1, vec_ok);
                 cp_async_commit();
             }
             // ---- B: level-0 rows row0-R .. row0+RY-1+R of this plane
             C inc[NR][V];
             {
-                const S *pl = stages + (size_t)slot * PLANE + l16 * V;
+                const S *pl = stages + (size_t)slot * SLOT + rdoff;
 #pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    int wrow = row0 - R + j;
-                    wrow = wrow < 0 ? 0 : (wrow >= WY ? WY - 1 : wrow);   // beyond the window: halo garbage
-                    ldsvec<DT>(pl + wrow * W, inc[j]);
-                }
-                if constexpr (MASK) {
+                for (int j = 0; j < NR; ++j) ldsvec<DT>(pl + j * W, inc[j]);
+                if constexpr (ZM) {
                     const bool zout = (unsigned)zin >= (unsigned)nz;
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) {
-                        const bool out = zout || (unsigned)(wsy + row0 - R + j) >= (unsigned)ny;
+                    for (int j = 0; j < NR; ++j)
 #pragma unroll
-                        for (int v = 0; v < V; ++v) inc[j][v] = (out || (need_cmask && !keep[v])) ? bval : inc[j][v];
-                    }
+                        for (int v = 0; v < V; ++v)
+                            inc[j][v] = (zout || ((yout_bits >> j) & 1u) || !keep[v]) ? bval : inc[j][v];
                 }
             }
             if constexpr (K == 1) {
-                __syncthreads();   // every warp has read the stage: refill it now
+                // every warp has read the stage: refill it now
+                if (__syncthreads_or(waitbad) && !bad) {
+                    bad = true;
+                    ibad = i;
+                }
                 if constexpr (PROD == PROD3_TMA) {
-                    if (threadIdx.x == 0 && i + F3_STAGES < nsp) {
+                    if (threadIdx.x == 0 && !bad && i + F3_STAGES < nsp) {
                         fence_proxy_async_smem();
-                        const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
-                        mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
-                        tma_load_3d(stages + (size_t)sl2 * PLANE, tmap, &bars[sl2], wsx, wsy, zi0 + i + F3_STAGES);
+                        const uint32_t g2 = g + F3_STAGES, sl2 = g2 % F3_STAGES;
+                        mbar_arrive_expect_tx(&bars[sl2], G::TMA_BYTES);
+                        tma_load_3d(stages + (size_t)sl2 * SLOT + R * W, tmap, &bars[sl2], wsx, wsy, zin + F3_STAGES);
                     }
                 }
             }
@@ -421,71 +472,83 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                         }
                     }
                 }
-                // emitted plane ze = J - R: Dirichlet cells keep the boundary value
+                // emitted plane ze = J - R; masked iterations: cells outside
+                // the domain keep the boundary value
                 const int ze = zin - (s + 1) * R;
-                if constexpr (MASK) {
+                if constexpr (ZM) {
                     const bool zout = (unsigned)ze >= (unsigned)nz;
 #pragma unroll
-                    for (int j = 0; j < RY; ++j) {
-                        const bool out = zout || (unsigned)(wsy + row0 + j) >= (unsigned)ny;
+                    for (int j = 0; j < RY; ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v)
-                            emit[j][v] = (out || (need_cmask && !keep[v])) ? bval : emit[j][v];
-                    }
+                            emit[j][v] = (zout || ((yout_bits >> (R + j)) & 1u) || !keep[v]) ? bval : emit[j][v];
                 }
                 if (s + 1 < K) {
-                    // publish the emitted rows; read the r rows above and below
-                    C *xb = xbuf + (size_t)xpar * PLANE + l16 * V;
+                    // publish the rows within R of the half-warp's edges (the
+                    // only ones other half-warps read); read the R rows above
+                    // and below -- another half-warp's or a guard row.  The
+                    // parity alternates per exchange and, U (K - 1) being
+                    // even, starts every group at 0.
+                    C *xb = xbuf + ((ph * (K - 1) + s) & 1) * G::XPLANE + rdoff;
 #pragma unroll
-                    for (int j = 0; j < RY; ++j) st_shared_vec<C, V>(xb + (row0 + j) * W, emit[j]);
-                    __syncthreads();
-                    if (s == 0 && PROD == PROD3_TMA && threadIdx.x == 0 && i + F3_STAGES < nsp) {
-                        // every warp has read this plane's stage: refill it
-                        fence_proxy_async_smem();
-                        const uint32_t g = gst + i + F3_STAGES, sl2 = g % F3_STAGES;
-                        mbar_arrive_expect_tx(&bars[sl2], G::STAGE_BYTES);
-                        tma_load_3d(stages + (size_t)sl2 * PLANE, tmap, &bars[sl2], wsx, wsy, zi0 + i + F3_STAGES);
+                    for (int j = 0; j < RY; ++j)
+                        if (j < R || j >= RY - R) st_shared_vec<C, V>(xb + (R + j) * W, emit[j]);
+                    if (s == 0) {
+                        if (__syncthreads_or(waitbad) && !bad) {
+                            bad = true;
+                            ibad = i;
+                        }
+                        if constexpr (PROD == PROD3_TMA) {
+                            if (threadIdx.x == 0 && !bad && i + F3_STAGES < nsp) {
+                                // every warp has read this plane's stage: refill it
+                                fence_proxy_async_smem();
+                                const uint32_t g2 = g + F3_STAGES, sl2 = g2 % F3_STAGES;
+                                mbar_arrive_expect_tx(&bars[sl2], G::TMA_BYTES);
+                                tma_load_3d(stages + (size_t)sl2 * SLOT + R * W, tmap, &bars[sl2], wsx, wsy,
+                                            zin + F3_STAGES);
+                            }
+                        }
+                    } else {
+                        __syncthreads();
                     }
 #pragma unroll
                     for (int j = 0; j < R; ++j) {
-                        const int ra = row0 - R + j, rb = row0 + RY + j;
-                        ld_shared_vec<C, V>(xb + (ra < 0 ? 0 : ra) * W, inc[j]);
-                        ld_shared_vec<C, V>(xb + (rb >= WY ? WY - 1 : rb) * W, inc[R + RY + j]);
-                        if constexpr (MASK) {
-                            // rows beyond the window that lie outside the domain
-                            const bool oa = (unsigned)(wsy + ra) >= (unsigned)ny || (unsigned)ze >= (unsigned)nz;
-                            const bool ob = (unsigned)(wsy + rb) >= (unsigned)ny || (unsigned)ze >= (unsigned)nz;
-#pragma unroll
-                            for (int v = 0; v < V; ++v) {
-                                inc[j][v] = oa ? bval : inc[j][v];
-                                inc[R + RY + j][v] = ob ? bval : inc[R + RY + j][v];
-                            }
-                        }
+                        ld_shared_vec<C, V>(xb + j * W, inc[j]);
+                        ld_shared_vec<C, V>(xb + (R + RY + j) * W, inc[R + RY + j]);
                     }
 #pragma unroll
                     for (int j = 0; j < RY; ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v) inc[R + j][v] = emit[j][v];
-                    xpar ^= 1;
-                } else if (ze >= zo0 && ze < zo1) {
+                } else if (!bad && ze >= zo0 && ze < zo1) {
                     // level K: store this half-warp's rows of the output tile
+                    S *op = orow + (int64_t)ze * pstride;
 #pragma unroll
                     for (int j = 0; j < RY; ++j) {
-                        const int y = wsy + row0 + j;
-                        if (y < osy || y >= oey) continue;
-                        S *rowp = dst + ((int64_t)ze * ny + y) * nx;
-                        if (vec_ok && xl >= osx && xl + V <= oex) {
-                            stvec<DT>(rowp + xl, emit[j]);
-                        } else {
+                        if (!((ystore >> j) & 1u)) continue;
+                        S *rp = op + (int64_t)j * nx;
+                        if (xvec) {
+                            stvec<DT>(rp, emit[j]);
+                        } else if (xsome) {
 #pragma unroll
                             for (int v = 0; v < V; ++v)
-                                if (xl + v >= osx && xl + v < oex) rowp[xl + v] = from_c<S>(emit[j][v]);
+                                if (xl + v >= osx && xl + v < oex) rp[v] = from_c<S>(emit[j][v]);
                         }
                     }
                 }
             }
         }
-        if (bad) break;
+    };
+
+    static_assert((U * (K - 1)) % 2 == 0, "exchange parity must restart every group");
+    for (int i0 = 0; i0 < nsp; i0 += U) {
+        if constexpr (MASK) {
+            const int zlo = zi0 + i0;
+            if (small || zlo < RK || zlo + U - 1 >= nz) group(std::true_type{}, i0);
+            else group(std::false_type{}, i0);
+        } else {
+            group(std::false_type{}, i0);
+        }
     }
     if (bad) {
         if (threadIdx.x == 0) {
@@ -514,15 +577,15 @@ __device__ __forceinline__ bool f3_interior(bool dir, int nx, int ny, int nz, in
 }
 
 template <int DT, int R, int PAT, int K, int RY, int PROD>
-__global__ void __launch_bounds__(F3_THREADS, 1)
+__global__ void __launch_bounds__((F3Geo<DT, R, K, RY>::THREADS), 1)
     fused3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F3Params<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
     using G = F3Geo<DT, R, K, RY>;
     extern __shared__ __align__(128) unsigned char smem[];
     S *stages = reinterpret_cast<S *>(smem);
-    C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::STAGE_BYTES + G::XBUF_BYTES);
+    C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::SLOT_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::SLOT_BYTES + G::XBUF_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = (int)p.g.n2, ny = (int)p.g.n1, nz = (int)p.g.n0;
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
@@ -533,12 +596,12 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             prefetch_tmap(&tmap);
         }
     }
+    f3_guard_init<DT, R, K, RY>(stages, xbuf, p.g.bval);
     __syncthreads();
     const C *wr = p.w;   // parameter space: the FMAs read the weights as constant operands
+    const bool small = p.ax.n < G::W || p.ay.n < G::WY;   // the window is larger than the grid
     uint32_t gst = 0;    // planes consumed so far by this CTA (stage ring position)
-    int xpar = 0;        // exchange-plane parity
     __shared__ unsigned long long s_ticket;
-    const int txy = p.ax.T * p.ay.T;
     // jobs are taken dynamically (faster SMs take more); the first and last z
     // ranges (Dirichlet edges) come first
     for (;;) {
@@ -556,15 +619,14 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
         f3_tile(p.ax, tx, osx, oex, wsx);
         f3_tile(p.ay, ty, osy, oey, wsy);
         const int zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
-        (void)txy;
         const bool ok = f3_interior<G::W, G::WY, R * K>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
             ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
                                                           nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
-                                                          zo0, zo1, p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane,
+                                                          zo0, zo1, p.vec_ok != 0, small, stages, xbuf, bars, gst, lane,
                                                           warp)
             : fused3d_job<DT, R, PAT, K, RY, PROD, true>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
                                                          nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
-                                                         zo0, zo1, p.vec_ok != 0, stages, xbuf, bars, gst, xpar, lane,
+                                                         zo0, zo1, p.vec_ok != 0, small, stages, xbuf, bars, gst, lane,
                                                          warp);
         if (!ok) {
             if (threadIdx.x == 0) record_status(p.status, kStatusTimeout);
@@ -588,7 +650,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
 // (about one second); a wait that gives up raises the abort flag and records
 // STENCIL_ERR_TIMEOUT.
 template <int DT, int R, int PAT, int K, int RY, int PROD>
-__global__ void __launch_bounds__(F3_THREADS, 1)
+__global__ void __launch_bounds__((F3Geo<DT, R, K, RY>::THREADS), 1)
     fused3d_mp_kernel(const __grid_constant__ CUtensorMap tm_src0, const __grid_constant__ CUtensorMap tm_even,
                       const __grid_constant__ CUtensorMap tm_odd,
                       const __grid_constant__ F3MpParams<typename Traits<DT>::C> p) {
@@ -597,8 +659,8 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     using G = F3Geo<DT, R, K, RY>;
     extern __shared__ __align__(128) unsigned char smem[];
     S *stages = reinterpret_cast<S *>(smem);
-    C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::STAGE_BYTES + G::XBUF_BYTES);
+    C *xbuf = reinterpret_cast<C *>(smem + F3_STAGES * G::SLOT_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + F3_STAGES * G::SLOT_BYTES + G::XBUF_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = (int)p.g.n2, ny = (int)p.g.n1, nz = (int)p.g.n0;
     const bool dir = p.g.bkind == STENCIL_DIRICHLET;
@@ -611,12 +673,13 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             prefetch_tmap(&tm_odd);
         }
     }
+    f3_guard_init<DT, R, K, RY>(stages, xbuf, p.g.bval);
     __syncthreads();
     MpCtl *ctl = p.ctl;
     int *done = p.done;
     const C *wr = p.w;
+    const bool small = p.ax.n < G::W || p.ay.n < G::WY;   // the window is larger than the grid
     uint32_t gst = 0;
-    int xpar = 0;
     const int txy = p.ax.T * p.ay.T;
     const int jobs = txy * p.chunks;
     const unsigned long long items = (unsigned long long)jobs * (unsigned)p.passes;
@@ -654,7 +717,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
             const TileSpan sz = tile_span(zo0 - RK, zo1 + RK, nz, p.Lz, !dir);
             const int cx = sx.count(), cxy = cx * sy.count(), nd = cxy * sz.count();
             bool ok = true;
-            for (int e = threadIdx.x; e < nd; e += F3_THREADS) {
+            for (int e = threadIdx.x; e < nd; e += G::THREADS) {
                 const int ex = sx.at(e % cx), ey = sy.at((e % cxy) / cx), ez = sz.at(e / cxy);
                 ok = ok && wait_counter(&done[(ez * p.ay.T + ey) * p.ax.T + ex], pass, &ctl->abort);
             }
@@ -676,11 +739,11 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
         S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
         const bool ok = f3_interior<G::W, G::WY, RK>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
             ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
-                                                          wsy, osy, oey, zo0, zo1, p.vec_ok != 0, stages, xbuf, bars,
-                                                          gst, xpar, lane, warp)
+                                                          wsy, osy, oey, zo0, zo1, p.vec_ok != 0, small, stages, xbuf,
+                                                          bars, gst, lane, warp)
             : fused3d_job<DT, R, PAT, K, RY, PROD, true>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
-                                                         wsy, osy, oey, zo0, zo1, p.vec_ok != 0, stages, xbuf, bars,
-                                                         gst, xpar, lane, warp);
+                                                         wsy, osy, oey, zo0, zo1, p.vec_ok != 0, small, stages, xbuf,
+                                                         bars, gst, lane, warp);
         if (!ok) {
             if (threadIdx.x == 0) {
                 atomicExch(&ctl->abort, 1);
@@ -701,7 +764,7 @@ __global__ void __launch_bounds__(F3_THREADS, 1)
     if (threadIdx.x == 0) s_last = worker_exit_is_last(&ctl->exited, gridDim.x);
     __syncthreads();
     if (s_last) {
-        for (int i = threadIdx.x; i < p.tiles; i += F3_THREADS) done[i] = 0;
+        for (int i = threadIdx.x; i < p.tiles; i += G::THREADS) done[i] = 0;
         if (threadIdx.x == 0) {
             ctl->ticket = 0ull;
             ctl->abort = 0;
@@ -722,9 +785,15 @@ inline int64_t f3_lz(int64_t nz, int64_t tiles, int64_t slots, int rk, int lz) {
     return (nz + best_c - 1) / best_c;
 }
 
-// Rows per half-warp: 2, or 1 where 2r k rows of y-halo would leave too
-// little of a 64-row window (and the partial planes too many registers).
-template <int DT, int R, int K> constexpr int f3_ry() { return R * K <= 4 ? 2 : 1; }
+// Rows per half-warp: 4 (8 warps, up to 255 registers a thread) for the
+// radius-1 star at K = 4, where fewer barriers and shared-memory accesses per
+// row outweigh the lower warp count; else 2 (16 warps, 128 registers).
+template <int DT, int R, int PAT, int K> constexpr int f3_ry() {
+    return R == 1 && PAT == STENCIL_STAR && K == 4 &&
+                   K * 2 * R * 4 * Traits<DT>::V * (int)(sizeof(typename Traits<DT>::C) / 4) <= 128
+               ? 4
+               : 2;
+}
 
 template <typename Prm>
 void f3_fill_common(const stencil_plan_s &P, Prm &p, int W, int H, int WY, int HY) {
@@ -745,7 +814,7 @@ template <int DT, int R, int PAT, int K>
 cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    constexpr int RY = f3_ry<DT, R, K>();
+    constexpr int RY = f3_ry<DT, R, PAT, K>();
     using G = F3Geo<DT, R, K, RY>;
     F3Params<C> p;
     f3_fill_common(P, p, G::W, G::H, G::WY, G::HY);
@@ -773,7 +842,7 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
         attr_done[tma ? 0 : 1] = true;
     }
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F3_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, G::THREADS, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     const int64_t tiles = (int64_t)p.ax.T * p.ay.T;
@@ -783,7 +852,7 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.chunks = (int)((nz + p.Lz - 1) / p.Lz);
     p.jobs = tiles * p.chunks;
     const int64_t grid = p.jobs < slots ? p.jobs : slots;
-    kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(map, p);
+    kern<<<(unsigned)grid, G::THREADS, smem, st>>>(map, p);
     return cudaGetLastError();
 }
 
@@ -792,7 +861,7 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
                           cudaStream_t st) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
-    constexpr int RY = f3_ry<DT, R, K>();
+    constexpr int RY = f3_ry<DT, R, PAT, K>();
     using G = F3Geo<DT, R, K, RY>;
     if (!fused3d_multi_ok(P, K) || passes < 1) return cudaErrorNotSupported;
     F3MpParams<C> p;
@@ -824,7 +893,7 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
         attr_done[tma ? 0 : 1] = true;
     }
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, F3_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, G::THREADS, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     const int64_t txy = (int64_t)p.ax.T * p.ay.T;
@@ -842,14 +911,15 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
     p.done = reinterpret_cast<int *>(static_cast<char *>(P.d_mp) + sizeof(MpCtl));
     const int64_t jobs = tiles * passes;
     const int64_t grid = jobs < slots ? jobs : slots;
-    kern<<<(unsigned)grid, F3_THREADS, smem, st>>>(maps[0], maps[1], maps[2], p);
+    kern<<<(unsigned)grid, G::THREADS, smem, st>>>(maps[0], maps[1], maps[2], p);
     return cudaGetLastError();
 }
 
-// Largest K instantiated for (dtype, r): bounded by the registers that hold
-// 2r partial planes per level (128 per thread at 512 threads).
+// Largest K instantiated for (dtype, r, pattern): bounded by the registers
+// that hold 2r partial planes per level (128 per thread at 512 threads); the
+// boxes of radius 2 and 3 have none (they run the plain sweep).
 template <int DT> constexpr int f3_kmax(int r, int pat) {
-    return r == 1 ? 4 : (r == 2 && pat == STENCIL_STAR) ? 2 : 1;
+    return pat == STENCIL_BOX && r > 1 ? 0 : r == 1 ? 4 : r == 2 ? 2 : 1;
 }
 
 template <int DT, int R, int PAT>
@@ -857,7 +927,7 @@ cudaError_t launch_f3mp_k(const stencil_plan_s &P, const void *src0, void *de, v
                           cudaStream_t st) {
     constexpr int KM = f3_kmax<DT>(R, PAT);
     switch (k) {
-        case 1: return launch_f3mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st);
+        case 1: if constexpr (KM >= 1) return launch_f3mp_t<DT, R, PAT, 1>(P, src0, de, dof, passes, st); break;
         case 2: if constexpr (KM >= 2) return launch_f3mp_t<DT, R, PAT, 2>(P, src0, de, dof, passes, st); break;
         case 3: if constexpr (KM >= 3) return launch_f3mp_t<DT, R, PAT, 3>(P, src0, de, dof, passes, st); break;
         case 4: if constexpr (KM >= 4) return launch_f3mp_t<DT, R, PAT, 4>(P, src0, de, dof, passes, st); break;
@@ -887,7 +957,7 @@ template <int DT, int R, int PAT>
 cudaError_t launch_f3_k(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st) {
     constexpr int KM = f3_kmax<DT>(R, PAT);
     switch (k) {
-        case 1: return launch_f3_t<DT, R, PAT, 1>(P, src, dst, st);
+        case 1: if constexpr (KM >= 1) return launch_f3_t<DT, R, PAT, 1>(P, src, dst, st); break;
         case 2: if constexpr (KM >= 2) return launch_f3_t<DT, R, PAT, 2>(P, src, dst, st); break;
         case 3: if constexpr (KM >= 3) return launch_f3_t<DT, R, PAT, 3>(P, src, dst, st); break;
         case 4: if constexpr (KM >= 4) return launch_f3_t<DT, R, PAT, 4>(P, src, dst, st); break;

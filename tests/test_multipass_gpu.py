@@ -202,7 +202,9 @@ def test_3d_int32_bit_exact(pattern, r, bkind):
             ref = oracle.run_int(3, r, pattern, shape, w, bkind, bval, u0, T)
             got = run(plan, x, T, k, FUSED).cpu().numpy()
             np.testing.assert_array_equal(got, ref, err_msg=f"{shape} k={k} T={T}")
-            assert sg.stencil_plan_launch_count(plan, T) == 1 + (T % k > 0)
+            # the 125-point box has no fused form: one plain launch per step
+            expect = T if (r == 2 and pattern == BOX) else 1 + (T % k > 0)
+            assert sg.stencil_plan_launch_count(plan, T) == expect
 
 
 @pytest.mark.parametrize("pattern", [STAR, BOX])
