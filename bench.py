@@ -750,6 +750,7 @@ def main():
             "vs_baseline": None, "dtype": dtn, "data": "synthetic (seeded uniform[0,1), fixed boundary)",
             "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T, "k": k,
                        "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan),
+                                 "block_warps": sg.stencil_plan_get_block_warps(plan),
                                  "launch": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass"}[variant]}
                        if tuned else None,
                        "l2": (f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush"

@@ -292,6 +292,15 @@ __host__ __device__ constexpr int max_c(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 __host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
 
+// 16-byte global -> shared copies (L2 only), grouped and waited for per group
+__device__ __forceinline__ void cp_async16(void *smem, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ int64_t wrap_idx(int64_t i, int64_t n) {
     int64_t m = i % n;
     return m < 0 ? m + n : m;

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "k_adjoint3d.cuh"
 #include "plan.h"
 
 namespace sg {
@@ -47,6 +48,7 @@ struct AdjParams {
 // (plane, row block) pairs) where the extents allow it, else the generic one.
 struct AdjShape {
     bool rows;
+    bool z3;               // the z-streamed 3D kernel (k_adjoint3d.cuh)
     dim3 grid, block;
     int nblocks;           // blocks = partial-sum slots
 };
@@ -310,6 +312,18 @@ constexpr int adj_rb(int d, int pat) { return d == 2 ? 2 : 1; }
 
 static AdjShape adj_shape(const stencil_plan_s &P) {
     AdjShape a;
+    a.z3 = false;
+    // 3D stencils of up to 27 points: the z-streamed kernel, two CTAs per SM
+    // at radius 1 (96 KB of planes each), one at radius 2 (142 KB)
+    if (P.dim == 3 && P.np <= 27 && P.n[0] < (1ll << 30) && P.n[1] < (1ll << 30) && P.n[2] < (1ll << 30) &&
+        (P.n[2] + A3_TX - 1) / A3_TX * ((P.n[1] + A3_TY - 1) / A3_TY) < (1ll << 30)) {
+        a.z3 = true;
+        a.rows = false;
+        a.nblocks = P.sm_count * (P.r == 1 ? 2 : 1);
+        a.grid = dim3((unsigned)a.nblocks, 1, 1);
+        a.block = dim3(A3_THREADS, 1, 1);
+        return a;
+    }
     const int64_t n0 = P.n[0], n1 = P.n[1], n2 = P.n[2], r = P.r;
     const int rb = adj_rb(P.dim, P.pattern);
     const int64_t groups = (n2 + ADJ_VX - 1) / ADJ_VX;
@@ -344,7 +358,41 @@ static cudaError_t launch_adj_t(const AdjParams &p, const AdjShape &a, cudaStrea
     return cudaGetLastError();
 }
 
+template <int R, int PAT>
+static cudaError_t launch_adj3_t(const Adj3Params &q, const AdjShape &a, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(adjoint3d_kernel<R, PAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             A3Geo<R>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    adjoint3d_kernel<R, PAT><<<a.grid, a.block, A3Geo<R>::SMEM, st>>>(q);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_adj(const stencil_plan_s &P, const AdjParams &p, const AdjShape &a, cudaStream_t st) {
+    if (a.z3) {
+        Adj3Params q;
+        q.lam_in = p.lam_in;
+        q.u = p.u;
+        q.lam_out = p.lam_out;
+        q.partials = p.partials;
+        q.nx = (int)P.n[2];
+        q.ny = (int)P.n[1];
+        q.nz = (int)P.n[0];
+        q.tiles_x = (int)((P.n[2] + A3_TX - 1) / A3_TX);
+        q.tiles_y = (int)((P.n[1] + A3_TY - 1) / A3_TY);
+        q.periodic = P.bkind == STENCIL_PERIODIC;
+        q.bval = p.bval;
+        q.first = p.first;
+        q.vec = p.vec_ok;
+        for (int j = 0; j < P.np; ++j) q.w[j] = p.w[j];
+        if (P.r == 1) return P.pattern == STENCIL_BOX ? launch_adj3_t<1, STENCIL_BOX>(q, a, st)
+                                                      : launch_adj3_t<1, STENCIL_STAR>(q, a, st);
+        if (P.r == 2 && P.pattern == STENCIL_STAR) return launch_adj3_t<2, STENCIL_STAR>(q, a, st);
+        return cudaErrorInvalidValue;
+    }
     const bool box = P.pattern == STENCIL_BOX;
 #define SG_ADJ(DD, RR)                                                                                  \
     if (P.dim == DD && P.r == RR) return box ? launch_adj_t<DD, RR, STENCIL_BOX>(p, a, st)              \
@@ -441,15 +489,40 @@ static stencil_status_t backward_from_ckpts(stencil_plan_s *P, const void *u0, c
     p.bval = (float)P->bval;
     p.partials = partials;
     for (int j = 0; j < P->np; ++j) p.w[j] = (float)P->w_eval[j];
+    // fused recompute where the plan's fused 3D kernel exists for this
+    // geometry and the tuner (if it ran) did not find the plain sweep faster
+    const bool all_levels = P->dim == 3 && P->r == 1 && fused3d_max_k(*P) >= 1 && !P->tuned_plain;
+    if (all_levels) {
+        stencil_status_t s = ensure_status_word(P);
+        if (s != STENCIL_OK) return s;
+    }
     const float *lam_next = static_cast<const float *>(grad_uT);
     int li = 0;
     bool first = true;
     for (int64_t m = M - 1; m >= 0; --m) {
         const int64_t t0 = m * c, t1 = std::min<int64_t>(T, t0 + c);
-        for (int64_t t = t0 + 1; t < t1; ++t) {
-            const void *src = (t - 1 == t0) ? ckpt(m) : seg((int)(t - 1 - t0));
-            stencil_status_t s = stencil_run(P, src, seg((int)(t - t0)), 1, stream);
-            if (s != STENCIL_OK) return s;
+        // the segment's inner states t0 + 1 .. t1 - 1: 3D radius-1 plans run
+        // fused passes of up to 4 steps that store every level; otherwise one
+        // step per launch
+        int64_t t = t0;
+        const void *src = ckpt(m);
+        while (t + 1 < t1) {
+            const int kk = (int)std::min<int64_t>(4, t1 - 1 - t);
+            void *lv[4] = {nullptr, nullptr, nullptr, nullptr};
+            for (int l = 0; l < kk; ++l) lv[l] = seg((int)(t + 1 + l - t0));
+            e = all_levels ? launch_f3_all_F32(*P, src, lv, kk, st) : cudaErrorNotSupported;
+            if (e == cudaErrorNotSupported) {
+                cudaGetLastError();
+                for (int l = 0; l < kk; ++l) {
+                    stencil_status_t s = stencil_run(P, l == 0 ? src : lv[l - 1], lv[l], 1, stream);
+                    if (s != STENCIL_OK) return s;
+                }
+            } else if (e != cudaSuccess) {
+                set_error(cudaGetErrorString(e));
+                return STENCIL_ERR_CUDA;
+            }
+            src = lv[kk - 1];
+            t += kk;
         }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             p.u = static_cast<const float *>(t == t0 ? ckpt(m) : seg((int)(t - t0)));

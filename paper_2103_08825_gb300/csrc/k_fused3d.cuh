@@ -135,6 +135,7 @@ template <typename C> struct F3Params {
     int vec_ok;
     int *status;
     JobCtl *ctl;            // job tickets (left at zero by the launch's last CTA)
+    void *lv[4];            // ALL: levels 1 .. K - 1 of the pass are stored here too
     C w[kMaxPts];           // evaluation order (read from the constant bank)
 };
 
@@ -167,13 +168,6 @@ template <typename C, int V> __device__ __forceinline__ void ld_shared_vec(const
         reinterpret_cast<uint4 *>(v)[i] = reinterpret_cast<const uint4 *>(p)[i];
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // Copy window plane z (virtual, wrapped or boundary) into a stage, every
 // thread a share, with 16-byte cp.async copies where a chunk is aligned and
@@ -290,9 +284,10 @@ __device__ __forceinline__ void f3_guard_init(typename Traits<DT>::S *stages, ty
 // (`small`), run a second instance of the loop body that resets every cell
 // outside the domain to the boundary value at every level.  Returns false if
 // a bounded wait gave up.
-template <int DT, int R, int PAT, int K, int RY, int PROD, bool MASK>
+template <int DT, int R, int PAT, int K, int RY, int PROD, bool MASK, bool ALL = false>
 __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typename Traits<DT>::S *__restrict__ src,
-                                            typename Traits<DT>::S *__restrict__ dst, int nx, int ny, int nz,
+                                            typename Traits<DT>::S *__restrict__ dst, void *const *lv, int nx, int ny,
+                                            int nz,
                                             bool dir, typename Traits<DT>::C bval, const typename Traits<DT>::C *wr,
                                             int wsx, int osx, int oex, int wsy, int osy, int oey, int zo0, int zo1,
                                             bool vec_ok, bool small, typename Traits<DT>::S *stages,
@@ -337,8 +332,24 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
     for (int j = 0; j < RY; ++j) ystore |= (wsy + row0 + j >= osy && wsy + row0 + j < oey) ? 1u << j : 0u;
     const bool xvec = vec_ok && xl >= osx && xl + V <= oex;
     const bool xsome = !xvec && xl + V > osx && xl < oex;   // part of the lane's columns
-    S *const orow = dst + (int64_t)(wsy + row0) * nx + xl;   // own first row, plane 0
+    const int64_t orow = (int64_t)(wsy + row0) * nx + xl;   // own first row, plane 0
     const int64_t pstride = (int64_t)nx * ny;
+    // this half-warp's rows of the output tile of plane ze into `base`
+    auto store_rows = [&](S *base, int ze, const C (&rows)[RY][V]) {
+        S *op = base + orow + (int64_t)ze * pstride;
+#pragma unroll
+        for (int j = 0; j < RY; ++j) {
+            if (!((ystore >> j) & 1u)) continue;
+            S *rp = op + (int64_t)j * nx;
+            if (xvec) {
+                stvec<DT>(rp, rows[j]);
+            } else if (xsome) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (xl + v >= osx && xl + v < oex) rp[v] = from_c<S>(rows[j][v]);
+            }
+        }
+    };
 
     // ---- prologue: first stages
     if constexpr (PROD == PROD3_TMA) {
@@ -520,21 +531,13 @@ __device__ __forceinline__ bool fused3d_job(const CUtensorMap *tmap, const typen
                     for (int j = 0; j < RY; ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v) inc[R + j][v] = emit[j][v];
+                    if constexpr (ALL) {
+                        // level s + 1 of the output tile, kept as well
+                        if (!bad && ze >= zo0 && ze < zo1) store_rows(static_cast<S *>(lv[s]), ze, emit);
+                    }
                 } else if (!bad && ze >= zo0 && ze < zo1) {
                     // level K: store this half-warp's rows of the output tile
-                    S *op = orow + (int64_t)ze * pstride;
-#pragma unroll
-                    for (int j = 0; j < RY; ++j) {
-                        if (!((ystore >> j) & 1u)) continue;
-                        S *rp = op + (int64_t)j * nx;
-                        if (xvec) {
-                            stvec<DT>(rp, emit[j]);
-                        } else if (xsome) {
-#pragma unroll
-                            for (int v = 0; v < V; ++v)
-                                if (xl + v >= osx && xl + v < oex) rp[v] = from_c<S>(emit[j][v]);
-                        }
-                    }
+                    store_rows(dst, ze, emit);
                 }
             }
         }
@@ -576,7 +579,7 @@ __device__ __forceinline__ bool f3_interior(bool dir, int nx, int ny, int nz, in
     return !dir || (wsx > 0 && wsx + W < nx && wsy > 0 && wsy + WY < ny && zo0 - RK >= 0 && zo1 + RK <= nz);
 }
 
-template <int DT, int R, int PAT, int K, int RY, int PROD>
+template <int DT, int R, int PAT, int K, int RY, int PROD, bool ALL = false>
 __global__ void __launch_bounds__((F3Geo<DT, R, K, RY>::THREADS), 1)
     fused3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ F3Params<typename Traits<DT>::C> p) {
     using S = typename Traits<DT>::S;
@@ -620,11 +623,11 @@ __global__ void __launch_bounds__((F3Geo<DT, R, K, RY>::THREADS), 1)
         f3_tile(p.ay, ty, osy, oey, wsy);
         const int zo0 = cz * p.Lz, zo1 = zo0 + p.Lz < nz ? zo0 + p.Lz : nz;
         const bool ok = f3_interior<G::W, G::WY, R * K>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
-            ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+            ? fused3d_job<DT, R, PAT, K, RY, PROD, false, ALL>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), p.lv,
                                                           nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
                                                           zo0, zo1, p.vec_ok != 0, small, stages, xbuf, bars, gst, lane,
                                                           warp)
-            : fused3d_job<DT, R, PAT, K, RY, PROD, true>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst),
+            : fused3d_job<DT, R, PAT, K, RY, PROD, true, ALL>(&tmap, static_cast<const S *>(p.src), static_cast<S *>(p.dst), p.lv,
                                                          nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex, wsy, osy, oey,
                                                          zo0, zo1, p.vec_ok != 0, small, stages, xbuf, bars, gst, lane,
                                                          warp);
@@ -738,10 +741,10 @@ __global__ void __launch_bounds__((F3Geo<DT, R, K, RY>::THREADS), 1)
         const CUtensorMap *tm = pass == 0 ? &tm_src0 : from_even ? &tm_even : &tm_odd;
         S *dst = static_cast<S *>(((p.passes - 1 - pass) & 1) == 0 ? p.dst_even : p.dst_odd);
         const bool ok = f3_interior<G::W, G::WY, RK>(dir, nx, ny, nz, wsx, wsy, zo0, zo1)
-            ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
+            ? fused3d_job<DT, R, PAT, K, RY, PROD, false>(tm, src, dst, nullptr, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
                                                           wsy, osy, oey, zo0, zo1, p.vec_ok != 0, small, stages, xbuf,
                                                           bars, gst, lane, warp)
-            : fused3d_job<DT, R, PAT, K, RY, PROD, true>(tm, src, dst, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
+            : fused3d_job<DT, R, PAT, K, RY, PROD, true>(tm, src, dst, nullptr, nx, ny, nz, dir, p.g.bval, wr, wsx, osx, oex,
                                                          wsy, osy, oey, zo0, zo1, p.vec_ok != 0, small, stages, xbuf,
                                                          bars, gst, lane, warp);
         if (!ok) {
@@ -810,8 +813,10 @@ void f3_fill_common(const stencil_plan_s &P, Prm &p, int W, int H, int WY, int H
     p.ay = f3_axis(P.n[1], WY, HY, dir);
 }
 
-template <int DT, int R, int PAT, int K>
-cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st) {
+// lv (ALL): levels 1 .. K - 1 of the pass are also stored, level l into lv[l - 1]
+template <int DT, int R, int PAT, int K, bool ALL = false>
+cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st,
+                        void *const *lv = nullptr) {
     using S = typename Traits<DT>::S;
     using C = typename Traits<DT>::C;
     constexpr int RY = f3_ry<DT, R, PAT, K>();
@@ -821,8 +826,10 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     p.src = src;
     p.dst = dst;
     p.ctl = static_cast<JobCtl *>(P.d_ctr);
+    for (int l = 0; l < 4; ++l) p.lv[l] = ALL && l < K - 1 ? lv[l] : nullptr;
     const int64_t nx = P.n[2], ny = P.n[1], nz = P.n[0];
     p.vec_ok = (nx % G::V == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+    for (int l = 0; l < K - 1; ++l) p.vec_ok = p.vec_ok && (!ALL || (uintptr_t)p.lv[l] % 16 == 0);
     bool tma = P.bkind == STENCIL_DIRICHLET && ((nx * (int64_t)sizeof(S)) % 16 == 0) && ((uintptr_t)src % 16 == 0);
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
@@ -833,7 +840,8 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
     }
     // cp.async path: 16-byte copies need 16-byte aligned rows
     if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
-    auto kern = tma ? fused3d_kernel<DT, R, PAT, K, RY, PROD3_TMA> : fused3d_kernel<DT, R, PAT, K, RY, PROD3_CPASYNC>;
+    auto kern = tma ? fused3d_kernel<DT, R, PAT, K, RY, PROD3_TMA, ALL>
+                    : fused3d_kernel<DT, R, PAT, K, RY, PROD3_CPASYNC, ALL>;
     const int smem = G::SMEM;
     static bool attr_done[2] = {false, false};
     if (!attr_done[tma ? 0 : 1]) {
@@ -976,6 +984,19 @@ cudaError_t launch_f3_dt(const stencil_plan_s &P, const void *src, void *dst, in
     if (P.r == 1) return launch_f3_r<DT, 1>(P, src, dst, k, st);
     if (P.r == 2) return launch_f3_r<DT, 2>(P, src, dst, k, st);
     if (P.r == 3) return launch_f3_r<DT, 3>(P, src, dst, k, st);
+    return cudaErrorInvalidValue;
+}
+
+// The pass of k <= 4 steps (radius 1) keeping every level: level l of
+// src into lv[l - 1], l = 1 .. k (the adjoint's recompute of a segment).
+template <int DT, int PAT>
+cudaError_t launch_f3_all_k(const stencil_plan_s &P, const void *src, void *const *lv, int k, cudaStream_t st) {
+    switch (k) {
+        case 1: return launch_f3_t<DT, 1, PAT, 1, true>(P, src, lv[0], st, lv);
+        case 2: return launch_f3_t<DT, 1, PAT, 2, true>(P, src, lv[1], st, lv);
+        case 3: return launch_f3_t<DT, 1, PAT, 3, true>(P, src, lv[2], st, lv);
+        case 4: return launch_f3_t<DT, 1, PAT, 4, true>(P, src, lv[3], st, lv);
+    }
     return cudaErrorInvalidValue;
 }
 

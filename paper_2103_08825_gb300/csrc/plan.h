@@ -93,6 +93,8 @@ cudaError_t launch_fused_multi(const stencil_plan_s &P, const void *src0, void *
 cudaError_t ensure_mp_state(const stencil_plan_s &P, int64_t tiles, cudaStream_t st);
 std::string fused2d_describe(const stencil_plan_s &P, int k);
 int fused3d_max_k(const stencil_plan_s &P);
+// one 3D FP32 radius-1 pass of k <= 4 steps storing every level (lv[l - 1] = level l)
+cudaError_t launch_f3_all_F32(const stencil_plan_s &P, const void *src, void *const *lv, int k, cudaStream_t st);
 cudaError_t launch_fused3d(const stencil_plan_s &P, const void *src, void *dst, int k, cudaStream_t st);
 std::string fused3d_describe(const stencil_plan_s &P, int k);
 int fused1d_max_k(const stencil_plan_s &P);
