@@ -53,9 +53,16 @@ WORKLOADS = {
 # capture, keyed by workload, k, tile length and a hash of the kernel sources
 # it was measured on; reported as null once those sources change.
 NCU_TRAFFIC = {
-    # 2D 5-point 8192^2 FP32, T = 64, k = 4, 64-row tiles: all 16 passes in one
-    # launch, read 5.039250 GB + write 4.251199 GB
-    "2d5p:k4:rows64:a76529d36e34ef8c": 9290449000,
+    # dram__bytes_read.sum + dram__bytes_write.sum of the dominant launch, one
+    # ncu capture each (profiles/launches_bench_2d5p_8192sq.md); the key names
+    # the workload, k, tile rows and a hash of the kernel sources, so an entry
+    # goes stale (null) as soon as the kernel changes.
+    # 2D 5-point 8192^2 FP32, T = 64, k = 4, 64-row tiles, the 16 passes in one
+    # launch: read 5.079726 GB + write 4.250656 GB (1.086x the algorithmic 8.590 GB)
+    "2d5p:k4:rows64:291387652b6d8ec6": 9330381568,
+    # 3D 7-point 512^3 FP32, T = 32, k = 4, 96-plane jobs, the 8 passes in one
+    # launch: read 4.814064 GB + write 4.274635 GB (1.058x the algorithmic 8.590 GB)
+    "3d7p:k4:rows96:b1c5a61e952c98e6": 9088698624,
 }
 
 CSRC = "paper_2103_08825_gb300/csrc/"
@@ -449,8 +456,12 @@ def run_adjoint(args):
         torch.cuda.synchronize()
         ew = float(np.max(np.abs(sgw.cpu().numpy() - ogw)) / np.max(np.abs(ogw)))
         eu = float(np.max(np.abs(sgu.cpu().numpy().astype(np.float64) - ogu)) / np.max(np.abs(ogu)))
+        # the uniform target makes lam = u_T - target change sign, so gw sums
+        # terms of both signs and cancels: the FP32 forward's rounding shows
+        # up relative to |gw| (the GPU test's bound for this target is 5e-3;
+        # without cancellation, target 0, it is 1e-5)
         err = {"kind": "GPU adjoint against the FP64 oracle adjoint on the 64^3 sample", "grad_w_normwise": ew,
-               "grad_u0_normwise": eu, "tolerance": {"grad_w": 1e-5, "grad_u0": 1e-4}}
+               "grad_u0_normwise": eu, "tolerance": {"grad_w": 5e-3, "grad_u0": 1e-4}}
     line = {"metric": "adjoint GStencil/s (backward from forward checkpoints) and backward/forward time",
             "value": upd / (ms_b * 1e-3) / 1e9, "unit": "GStencil/s", "n_gpus": 1, "dtype": "f32",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,

@@ -143,6 +143,11 @@ __device__ __forceinline__ void a3_load_fast(float *slot, const float *__restric
     }
 }
 
+__device__ __forceinline__ void a3_ld4(const float *p, float (&r)[4]) {
+    const float4 m = *reinterpret_cast<const float4 *>(p);
+    r[0] = m.x; r[1] = m.y; r[2] = m.z; r[3] = m.w;
+}
+
 // 12 values of a slot row around a thread's 4 columns: r[i] = column xl - 4 + i
 // (NEEDX), else only r[4..7]
 template <bool NEEDX>
@@ -179,6 +184,7 @@ __global__ void __launch_bounds__(A3_THREADS, 2) adjoint3d_kernel(const __grid_c
     int64_t u = units * blockIdx.x / gridDim.x;
     const int64_t uend = units * (blockIdx.x + 1) / gridDim.x;
     int nplanes_done = 0;   // planes since the last FP64 flush
+    float lamC[3][A3_RY][4], uC[3][A3_RY][4];   // the 7-point star's centre rows of planes z - 1 .. z + 1
     while (u < uend) {
         const int tile = (int)(u / p.nz), z0 = (int)(u % p.nz);
         const int64_t zend = z0 + (uend - u);
@@ -215,63 +221,167 @@ __global__ void __launch_bounds__(A3_THREADS, 2) adjoint3d_kernel(const __grid_c
                 cp_async_commit();
             }
             const int z = z0 + t;
+            if constexpr (PAT == STENCIL_STAR && R == 1) {
+                // The 7-point star: centre rows of planes z - 1, z, z + 1 stay
+                // in registers (C[0..2], rotated one plane per step, so each
+                // plane's centre rows are read from shared memory once); the
+                // rows above and below come from the slot, x-neighbours by
+                // shuffles (the half-warp's edge lanes read the slot's halo
+                // columns).
+                const int rbase = (hw * A3_RY + R) * A3_XW + A3_XH + xl;   // own first row in a slot
+                if (t == 0) {
 #pragma unroll
-            for (int b = 0; b < A3_RY; ++b) {
-                const int yl = hw * A3_RY + b;        // tile row
-                const int y = y0 + yl, xg = x0 + xl;
-                const int rowoff = (yl + R) * A3_XW + A3_XH + xl;
-                // lam at this thread's own points; 0 for points outside the grid
-                float lc[4];
-                {
-                    const float4 m = *reinterpret_cast<const float4 *>(lam_ring + ((t + R) % NSL) * SLOT + rowoff);
-                    lc[0] = m.x; lc[1] = m.y; lc[2] = m.z; lc[3] = m.w;
-                    const bool yin = y < p.ny;
+                    for (int q = 0; q < 2; ++q)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) lc[v] = (yin && xg + v < p.nx) ? lc[v] : 0.f;
-                }
-                float acc[4];
-                bool first = true;
-#pragma unroll
-                for (int oz = -R; oz <= R; ++oz) {
-                    const float *ls = lam_ring + ((t + R - oz) % NSL) * SLOT;   // plane z - oz
-                    const float *us = u_ring + ((t + R + oz) % NSL) * SLOT;     // plane z + oz
-#pragma unroll
-                    for (int oy = -R; oy <= R; ++oy) {
-                        bool any = false;
-#pragma unroll
-                        for (int ox = -R; ox <= R; ++ox) any = any || Sh::inc(oz, oy, ox);
-                        if (!any) continue;
-                        float lr[12], ur[12];
-                        if (PAT == STENCIL_BOX || (oz == 0 && oy == 0)) {
-                            a3_row<true>(ls + rowoff - oy * A3_XW, lr);
-                            a3_row<true>(us + rowoff + oy * A3_XW, ur);
-                        } else {
-                            a3_row<false>(ls + rowoff - oy * A3_XW, lr);
-                            a3_row<false>(us + rowoff + oy * A3_XW, ur);
+                        for (int b = 0; b < A3_RY; ++b) {
+                            a3_ld4(lam_ring + ((t + q) % NSL) * SLOT + rbase + b * A3_XW, lamC[q][b]);
+                            a3_ld4(u_ring + ((t + q) % NSL) * SLOT + rbase + b * A3_XW, uC[q][b]);
                         }
+                }
 #pragma unroll
-                        for (int ox = -R; ox <= R; ++ox) {
-                            if (!Sh::inc(oz, oy, ox)) continue;
-                            const int j = Sh::widx(oz, oy, ox);
-                            const float w = p.w[j];
+                for (int b = 0; b < A3_RY; ++b) {
+                    a3_ld4(lam_ring + ((t + 2) % NSL) * SLOT + rbase + b * A3_XW, lamC[2][b]);
+                    a3_ld4(u_ring + ((t + 2) % NSL) * SLOT + rbase + b * A3_XW, uC[2][b]);
+                }
+                const float *lz = lam_ring + ((t + 1) % NSL) * SLOT + rbase;
+                const float *uz = u_ring + ((t + 1) % NSL) * SLOT + rbase;
+                float lup[4], ldn[4], uup[4], udn[4];
+                a3_ld4(lz - A3_XW, lup);
+                a3_ld4(lz + A3_RY * A3_XW, ldn);
+                a3_ld4(uz - A3_XW, uup);
+                a3_ld4(uz + A3_RY * A3_XW, udn);
+                float lL[A3_RY], lR[A3_RY], uL[A3_RY], uR[A3_RY];
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                const float l = lr[4 + v - ox];   // lam(x - o)
-                                acc[v] = first ? __fmul_rn(w, l) : __fmaf_rn(w, l, acc[v]);
-                                gw[j] = __fmaf_rn(lc[v], ur[4 + v + ox], gw[j]);   // lam(x) u(x + o)
+                for (int b = 0; b < A3_RY; ++b) {
+                    lL[b] = __shfl_up_sync(0xffffffffu, lamC[1][b][3], 1, 16);
+                    lR[b] = __shfl_down_sync(0xffffffffu, lamC[1][b][0], 1, 16);
+                    uL[b] = __shfl_up_sync(0xffffffffu, uC[1][b][3], 1, 16);
+                    uR[b] = __shfl_down_sync(0xffffffffu, uC[1][b][0], 1, 16);
+                    if ((lane & 15) == 0) {
+                        lL[b] = lz[b * A3_XW - 1];
+                        uL[b] = uz[b * A3_XW - 1];
+                    }
+                    if ((lane & 15) == 15) {
+                        lR[b] = lz[b * A3_XW + 4];
+                        uR[b] = uz[b * A3_XW + 4];
+                    }
+                }
+                // the value at (plane z + dz, row b + dy, column v + dx)
+                auto at = [&](const float (&Cc)[3][A3_RY][4], const float (&up)[4], const float (&dn)[4],
+                              const float (&L)[A3_RY], const float (&Rr)[A3_RY], int b, int dz, int dy, int dx,
+                              int v) -> float {
+                    if (dz != 0) return Cc[1 + dz][b][v];
+                    if (dy != 0) {
+                        const int bb = b + dy;
+                        return bb < 0 ? up[v] : (bb >= A3_RY ? dn[v] : Cc[1][bb][v]);
+                    }
+                    const int vv = v + dx;
+                    return vv < 0 ? L[b] : (vv >= 4 ? Rr[b] : Cc[1][b][vv]);
+                };
+#pragma unroll
+                for (int b = 0; b < A3_RY; ++b) {
+                    const int y = y0 + hw * A3_RY + b, xg = x0 + xl;
+                    float lc[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) lc[v] = (y < p.ny && xg + v < p.nx) ? lamC[1][b][v] : 0.f;
+                    float acc[4];
+                    bool first = true;
+#pragma unroll
+                    for (int oz = -R; oz <= R; ++oz)
+#pragma unroll
+                        for (int oy = -R; oy <= R; ++oy)
+#pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) {
+                                if (!Sh::inc(oz, oy, ox)) continue;
+                                const int j = Sh::widx(oz, oy, ox);
+                                const float w = p.w[j];
+#pragma unroll
+                                for (int v = 0; v < 4; ++v) {
+                                    const float l = at(lamC, lup, ldn, lL, lR, b, -oz, -oy, -ox, v);   // lam(x - o)
+                                    acc[v] = first ? __fmul_rn(w, l) : __fmaf_rn(w, l, acc[v]);
+                                    gw[j] = __fmaf_rn(lc[v], at(uC, uup, udn, uL, uR, b, oz, oy, ox, v), gw[j]);
+                                }
+                                first = false;
                             }
-                            first = false;
+                    if (y < p.ny) {
+                        float *out = p.lam_out + ((size_t)z * p.ny + y) * p.nx + xg;
+                        if (p.vec && xg + 4 <= p.nx) {
+                            *reinterpret_cast<float4 *>(out) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                if (xg + v < p.nx) out[v] = acc[v];
                         }
                     }
                 }
-                if (y < p.ny) {
-                    float *out = p.lam_out + ((size_t)z * p.ny + y) * p.nx + xg;
-                    if (p.vec && xg + 4 <= p.nx) {
-                        *reinterpret_cast<float4 *>(out) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                    } else {
 #pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            if (xg + v < p.nx) out[v] = acc[v];
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int b = 0; b < A3_RY; ++b)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            lamC[q][b][v] = lamC[q + 1][b][v];
+                            uC[q][b][v] = uC[q + 1][b][v];
+                        }
+            } else {
+    #pragma unroll
+                for (int b = 0; b < A3_RY; ++b) {
+                    const int yl = hw * A3_RY + b;        // tile row
+                    const int y = y0 + yl, xg = x0 + xl;
+                    const int rowoff = (yl + R) * A3_XW + A3_XH + xl;
+                    // lam at this thread's own points; 0 for points outside the grid
+                    float lc[4];
+                    {
+                        const float4 m = *reinterpret_cast<const float4 *>(lam_ring + ((t + R) % NSL) * SLOT + rowoff);
+                        lc[0] = m.x; lc[1] = m.y; lc[2] = m.z; lc[3] = m.w;
+                        const bool yin = y < p.ny;
+    #pragma unroll
+                        for (int v = 0; v < 4; ++v) lc[v] = (yin && xg + v < p.nx) ? lc[v] : 0.f;
+                    }
+                    float acc[4];
+                    bool first = true;
+    #pragma unroll
+                    for (int oz = -R; oz <= R; ++oz) {
+                        const float *ls = lam_ring + ((t + R - oz) % NSL) * SLOT;   // plane z - oz
+                        const float *us = u_ring + ((t + R + oz) % NSL) * SLOT;     // plane z + oz
+    #pragma unroll
+                        for (int oy = -R; oy <= R; ++oy) {
+                            bool any = false;
+    #pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) any = any || Sh::inc(oz, oy, ox);
+                            if (!any) continue;
+                            float lr[12], ur[12];
+                            if (PAT == STENCIL_BOX || (oz == 0 && oy == 0)) {
+                                a3_row<true>(ls + rowoff - oy * A3_XW, lr);
+                                a3_row<true>(us + rowoff + oy * A3_XW, ur);
+                            } else {
+                                a3_row<false>(ls + rowoff - oy * A3_XW, lr);
+                                a3_row<false>(us + rowoff + oy * A3_XW, ur);
+                            }
+    #pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) {
+                                if (!Sh::inc(oz, oy, ox)) continue;
+                                const int j = Sh::widx(oz, oy, ox);
+                                const float w = p.w[j];
+    #pragma unroll
+                                for (int v = 0; v < 4; ++v) {
+                                    const float l = lr[4 + v - ox];   // lam(x - o)
+                                    acc[v] = first ? __fmul_rn(w, l) : __fmaf_rn(w, l, acc[v]);
+                                    gw[j] = __fmaf_rn(lc[v], ur[4 + v + ox], gw[j]);   // lam(x) u(x + o)
+                                }
+                                first = false;
+                            }
+                        }
+                    }
+                    if (y < p.ny) {
+                        float *out = p.lam_out + ((size_t)z * p.ny + y) * p.nx + xg;
+                        if (p.vec && xg + 4 <= p.nx) {
+                            *reinterpret_cast<float4 *>(out) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                        } else {
+    #pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                if (xg + v < p.nx) out[v] = acc[v];
+                        }
                     }
                 }
             }
