@@ -219,6 +219,24 @@ stencil_status_t stencil_inplace_workspace_bytes(stencil_plan_t plan, int64_t *b
 stencil_status_t stencil_run_vc(stencil_plan_t plan, const void *coef, const void *u_in, void *u_out, int64_t T,
                                 void *stream);
 
+/* Reverse-mode derivative of stencil_run_vc (not in the paper: neither the
+ * coefficient fields nor the derivative are).  For lam_T = grad_uT = dL/du_T
+ * of a loss L of u_T = T steps applied to u0 with coefficient field `coef`:
+ *     grad_coef[o][x] = dL/dc_o[x] = sum_t lam_{t+1}[x] * u_t(x + o)
+ *                       (the boundary value where x + o lies outside a Dirichlet domain)
+ *     lam_t[y]        = sum_o c_o[y - o] * lam_{t+1}[y - o]
+ *                       (y - o wrapped on periodic axes, dropped outside a Dirichlet domain)
+ *     grad_u0         = lam_0.
+ * F32 and F64 plans, d = 1..3.  coef and grad_coef: np x N values in the
+ * plan's arithmetic type, compact offset order (stencil_run_vc's layout);
+ * grad_coef is overwritten.  The forward states come from checkpoints every
+ * ckpt_every steps (1..T) taken by a forward sweep inside the call, each
+ * segment's inner states recomputed one step at a time; the workspace
+ * (ceil(T / ckpt_every) + ckpt_every grids) is plan-owned.  grad_uT, grad_u0,
+ * u0 must not overlap each other or coef.  Enqueued on `stream`. */
+stencil_status_t stencil_adjoint_vc(stencil_plan_t plan, const void *coef, const void *u0, const void *grad_uT,
+                                    int64_t T, int32_t ckpt_every, void *grad_u0, void *grad_coef, void *stream);
+
 /* Many host grids in a row, pipelined: h_out[i] := T steps applied to
  * h_in[i] for i < n (host buffers of the plan's shape and dtype, each read or
  * written during the call).  Two input and two output grids are kept on the

@@ -32,7 +32,7 @@ EXPORTS = [
     "stencil_plan_get_tile_rows", "stencil_plan_set_block_warps", "stencil_plan_get_block_warps",
     "stencil_plan_tune", "stencil_plan_launch_count",
     "stencil_plan_describe", "stencil_run", "stencil_run_host", "stencil_run_host_many", "stencil_run_inplace",
-    "stencil_inplace_workspace_bytes", "stencil_run_vc", "stencil_batch_create",
+    "stencil_inplace_workspace_bytes", "stencil_run_vc", "stencil_adjoint_vc", "stencil_batch_create",
     "stencil_batch_destroy", "stencil_batch_run", "stencil_batch_get_device_status", "stencil_batch_set_config",
     "stencil_batch_get_config", "stencil_batch_tune",
     "stencil_batch_launch_count", "stencil_adjoint_run", "stencil_run_checkpointed",
@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "stencil_run_host_many": (st, [vp, i64, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, vp]),
         "stencil_inplace_workspace_bytes": (st, [vp, ctypes.POINTER(i64)]),
         "stencil_run_vc": (st, [vp, vp, vp, vp, i64, vp]),
+        "stencil_adjoint_vc": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
         "stencil_batch_create": (st, [ctypes.POINTER(vp), i32, i32, i32, ctypes.POINTER(i64),
                                       ctypes.POINTER(stencil_weights_t), ctypes.POINTER(i64),
                                       ctypes.POINTER(stencil_boundary_t), i32]),
@@ -299,6 +300,32 @@ def stencil_run_vc(plan: Plan, coef, u_in, u_out, T: int, stream=None):
                                  ctypes.c_void_p(u_out.data_ptr()), int(T), _stream_handle(stream)), "stencil_run_vc")
     return u_out
 
+
+
+def stencil_adjoint_vc(plan: Plan, coef, u0, grad_uT, T: int, ckpt_every: int, grad_u0=None, grad_coef=None,
+                       stream=None):
+    """(grad_u0, grad_coef) of the variable-coefficient sweep for lam_T =
+    grad_uT (F32 / F64 plans); grad_coef has coef's shape and dtype."""
+    import torch
+    _check_grid(plan, u0, "u0")
+    _check_grid(plan, grad_uT, "grad_uT")
+    ctype = {STENCIL_F32: torch.float32, STENCIL_F64: torch.float64}.get(plan.dtype)
+    if ctype is None:
+        raise ValueError("the variable-coefficient adjoint supports F32 and F64 plans")
+    if (not coef.is_cuda or not coef.is_contiguous() or coef.dtype != ctype or coef.device != u0.device
+            or tuple(coef.shape) != (len(plan.weights),) + plan.shape):
+        raise ValueError("coef must be a contiguous CUDA tensor of shape (npoints, *shape) in the arithmetic type")
+    grad_u0 = torch.empty_like(u0) if grad_u0 is None else grad_u0
+    grad_coef = torch.empty_like(coef) if grad_coef is None else grad_coef
+    _check_grid(plan, grad_u0, "grad_u0")
+    if grad_coef.shape != coef.shape or grad_coef.dtype != coef.dtype or not grad_coef.is_contiguous() \
+            or grad_coef.device != coef.device:
+        raise ValueError("grad_coef must be a contiguous tensor like coef")
+    _check(load().stencil_adjoint_vc(plan.handle, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(u0.data_ptr()),
+                                     ctypes.c_void_p(grad_uT.data_ptr()), int(T), int(ckpt_every),
+                                     ctypes.c_void_p(grad_u0.data_ptr()), ctypes.c_void_p(grad_coef.data_ptr()),
+                                     _stream_handle(stream)), "stencil_adjoint_vc")
+    return grad_u0, grad_coef
 
 def stencil_run_host(plan: Plan, h_in, h_out, T: int, stream=None):
     """Host-buffer run (numpy arrays or CPU tensors); synchronises."""

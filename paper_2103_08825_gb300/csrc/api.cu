@@ -297,6 +297,7 @@ stencil_status_t stencil_plan_destroy(stencil_plan_t P) {
     cudaFree(P->hws[1]);
     cudaFree(P->d_status);
     cudaFree(P->adj_ws);
+    cudaFree(P->vcadj_ws);
     cudaFree(P->adj_partials);
     cudaFree(P->d_mp);
     cudaFree(P->inpl_ws);

@@ -54,6 +54,8 @@ struct stencil_plan_s {
     size_t ckpt_ws_bytes = 0;
     void *adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
+    void *vcadj_ws = nullptr;   // variable-coefficient adjoint: checkpoints, segment states, lam grids
+    size_t vcadj_ws_bytes = 0;
     double *adj_partials = nullptr;
     size_t adj_partials_n = 0;
 };
