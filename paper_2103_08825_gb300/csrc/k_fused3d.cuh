@@ -813,6 +813,18 @@ void f3_fill_common(const stencil_plan_s &P, Prm &p, int W, int H, int WY, int H
     p.ay = f3_axis(P.n[1], WY, HY, dir);
 }
 
+// x halo of a TMA-fed Dirichlet grid: with boundary-aware tiling the windows
+// start at 0, at multiples of the tile width B = W - 2h and at n - W, so only
+// B (and n, which TMA already needs) must be 16-byte multiples -- the halo
+// itself need not be (a 4-column halo instead of 8 for 2-byte types).  The
+// periodic and cp.async paths keep G::H, a 16-byte multiple (their windows
+// start h before each tile).
+inline int f3_hx(int rk, int W, int al) {
+    int h = rk;
+    while ((W - 2 * h) % al != 0) ++h;
+    return h;
+}
+
 // lv (ALL): levels 1 .. K - 1 of the pass are also stored, level l into lv[l - 1]
 template <int DT, int R, int PAT, int K, bool ALL = false>
 cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cudaStream_t st,
@@ -838,6 +850,7 @@ cudaError_t launch_f3_t(const stencil_plan_s &P, const void *src, void *dst, cud
         const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)G::WY, 1u};
         tma = make_tmap(&map, DT, 3, dims, box, src);
     }
+    if (tma) f3_fill_common(P, p, G::W, f3_hx(R * K, G::W, G::AL), G::WY, G::HY);
     // cp.async path: 16-byte copies need 16-byte aligned rows
     if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
     auto kern = tma ? fused3d_kernel<DT, R, PAT, K, RY, PROD3_TMA, ALL>
@@ -890,6 +903,7 @@ cudaError_t launch_f3mp_t(const stencil_plan_s &P, const void *src0, void *dst_e
         const void *bases[3] = {src0, dst_even, dst_odd};
         for (int i = 0; i < 3 && tma; ++i) tma = make_tmap(&maps[i], DT, 3, dims, box, bases[i]);
     }
+    if (tma) f3_fill_common(P, p, G::W, f3_hx(R * K, G::W, G::AL), G::WY, G::HY);
     if (!tma) p.vec_ok = p.vec_ok && ((nx * (int64_t)sizeof(S)) % 16 == 0);
     auto kern = tma ? fused3d_mp_kernel<DT, R, PAT, K, RY, PROD3_TMA>
                     : fused3d_mp_kernel<DT, R, PAT, K, RY, PROD3_CPASYNC>;
