@@ -487,6 +487,9 @@ def main():
     ap.add_argument("--workload", default="2d5p", choices=sorted(WORKLOADS) + ["batch", "adjoint"])
     ap.add_argument("--k", type=int, default=0, help="fusion depth (0 = autotune)")
     ap.add_argument("--tile-rows", type=int, default=0, help="2D tile height with --k (0 = the plan's default)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "fused", "per_pass", "tess"],
+                    help="launch form with --k: persistent fused, one launch per pass, or tessellate tiling "
+                         "(time tiles of k levels; --tile-rows = tile extent)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=0, help="steps for the plain sweep (0 = steps/4)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -541,6 +544,10 @@ def main():
     if args.k > 0:
         sg.stencil_plan_set_k(plan, args.k)
         sg.stencil_plan_set_tile_rows(plan, args.tile_rows)
+        if args.variant != "auto":
+            sg.stencil_plan_set_variant(plan, {"fused": sg.STENCIL_VARIANT_FUSED,
+                                               "per_pass": sg.STENCIL_VARIANT_FUSED_PER_PASS,
+                                               "tess": sg.STENCIL_VARIANT_TESSELLATE}[args.variant])
         tuned = None
     else:
         tuned = sg.stencil_plan_tune(plan, p.T)
@@ -760,9 +767,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtn, "data": "synthetic (seeded uniform[0,1), fixed boundary)",
             "config": {"workload": workload_name(args.workload, p), "grid": list(p.shape), "T": p.T, "k": k,
+                       "launch_form": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass",
+                                       3: "tessellate"}[variant],
                        "tuned": {"k": tuned[0], "ms": tuned[1], "tile_rows": sg.stencil_plan_get_tile_rows(plan),
                                  "block_warps": sg.stencil_plan_get_block_warps(plan),
-                                 "launch": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass"}[variant]}
+                                 "launch": {0: "persistent multi-pass", 1: "plain", 2: "one launch per pass",
+                                            3: "tessellate"}[variant]}
                        if tuned else None,
                        "l2": (f"inputs larger than L2 ({p.npts * esize / 2**20:.0f} MiB per grid); no flush"
                               if not flush_l2 else
