@@ -223,11 +223,16 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     using G = F2Geo<DT, R, K>;
     using Sh = Shape<2, R, PAT>;
     constexpr int V = G::V, W = G::W, H = G::H, BW = G::BW, NS = 2 * R;
-    // step unroll: the partial-row slots repeat every 2R rows, the register
-    // prefetch ring (PROD_REG) every F2_PREF rows and the TMA stages every
-    // F2_ROWS rows: U = lcm(2R, F2_PREF) (4 for r <= 2, 12 for r = 3)
-    constexpr int U = lcm_c(NS, F2_PREF);
-    static_assert(U % NS == 0 && U % F2_PREF == 0 && U % F2_ROWS == 0, "unroll");
+    // step unroll: the partial-row slots repeat every 2R rows and the register
+    // prefetch ring (PROD_REG) every F2_PREF rows: U = lcm(2R, F2_PREF) (4 for
+    // r <= 2, 12 for r = 3).  The position within a TMA stage of F2_ROWS rows
+    // is a run-time index, so box stencils fed by TMA unroll only U = 2R: half
+    // the code of their (large) loop body for r = 1, whose instruction fetch
+    // limited it (2D9P +6 %); the star keeps the longer unroll (2D5P -3 % with
+    // the short one)
+    constexpr int U = PROD == PROD_TMA && PAT == STENCIL_BOX ? NS : lcm_c(NS, F2_PREF);
+    static_assert(U % NS == 0 && (PROD == PROD_TMA || U % F2_PREF == 0), "unroll");
+    static_assert((F2_ROWS & (F2_ROWS - 1)) == 0, "stage rows: a power of two");
     constexpr uint32_t FULLM = (1u << V) - 1u;
 
     // row indices fit in 32 bits (checked by the launcher)
@@ -283,8 +288,9 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
     for (int i0 = 0; i0 < nsp; i0 += U) {
 #pragma unroll
         for (int ph = 0; ph < U; ++ph) {
+        const int rr = (i0 + ph) & (F2_ROWS - 1);   // row within the TMA stage
         if constexpr (PROD == PROD_TMA) {
-            if (ph % F2_ROWS == 0) {
+            if (rr == 0) {
                 const bool ok = mbar_wait_bounded(&bars[slot], par);
                 if (__any_sync(0xffffffffu, !ok)) {
                     // give up: wait (bounded, about ten seconds per stage) for
@@ -306,7 +312,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
             const int yin = yi0 + i;
             C cur[V];
             if constexpr (PROD == PROD_TMA) {
-                ldsvec<DT>(srow + (ph % F2_ROWS) * W, cur);
+                ldsvec<DT>(srow + rr * W, cur);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) cur[v] = ring[ph % F2_PREF][v];
@@ -395,7 +401,7 @@ __device__ __forceinline__ bool fused2d_job(const CUtensorMap *tmap, const typen
             }
         }
         if constexpr (PROD == PROD_TMA) {
-            if (ph % F2_ROWS == F2_ROWS - 1) {
+            if (rr == F2_ROWS - 1) {
                 // stage consumed by every lane: refill it with the stage S ahead
                 __syncwarp();
                 if (lane == 0 && q + F2_STAGES < nst) {

@@ -56,6 +56,13 @@ stencil_status_t tess_run(stencil_plan_s *P, const void *u_in, void *u_out, int6
         set_error("tessellation needs every extent >= 2 h r (h = the plan's k)");
         return STENCIL_ERR_UNSUPPORTED;
     }
+    // a tile (segments shorter than 2b, or the whole axis) indexes its points in 32 bits
+    int64_t tile_pts = 1;
+    for (int a = 0; a < 3; ++a) tile_pts *= std::min<int64_t>(g.ax[a].n, 2 * (int64_t)g.ax[a].b);
+    if (tile_pts >= (1ll << 31)) {
+        set_error("tessellation tile too large (tile extent^d must stay below 2^31 points)");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
     stencil_status_t s = ensure_buf(&P->ws, P->grid_bytes);
     if (s != STENCIL_OK) return s;
     void *buf[2];

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) tess_kernel(const __grid_constant__ TessP
             const S *__restrict__ src = static_cast<const S *>(p.buf[(p.t0 + t - 1) & 1]);
             S *__restrict__ dst = static_cast<S *>(p.buf[(p.t0 + t) & 1]);
             int lo[3], hi[3];
-            int64_t ext = 1;
+            int ext = 1;   // points of the tile at this level (a tile is at most a few 10^4 points)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (a < 3 - D) {
@@ -151,10 +151,13 @@ __global__ void __launch_bounds__(256) tess_kernel(const __grid_constant__ TessP
                 ext *= hi[a] > lo[a] ? hi[a] - lo[a] : 0;
             }
             const int e1 = hi[1] - lo[1], e2 = hi[2] - lo[2];
-            for (int64_t q = threadIdx.x; q < ext; q += blockDim.x) {
-                int i2 = lo[2] + (int)(q % e2);
-                const int64_t qq = q / e2;
-                int i1 = lo[1] + (int)(qq % e1), i0 = lo[0] + (int)(qq / e1);
+            for (int q = threadIdx.x; q < ext; q += blockDim.x) {
+                // 32-bit index arithmetic: a 64-bit division per point cost
+                // more than the stencil itself
+                const int qq = q / e2;
+                int i2 = lo[2] + (q - qq * e2);
+                const int q1 = qq / e1;
+                int i1 = lo[1] + (qq - q1 * e1), i0 = lo[0] + q1;
                 // virtual coordinates of a wrapping inverted range
                 if (i0 < 0) i0 += n0; else if (i0 >= n0) i0 -= n0;
                 if (i1 < 0) i1 += n1; else if (i1 >= n1) i1 -= n1;
