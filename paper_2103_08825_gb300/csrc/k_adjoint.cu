@@ -314,7 +314,7 @@ static AdjShape adj_shape(const stencil_plan_s &P) {
     AdjShape a;
     a.z3 = false;
     // 3D stencils of up to 27 points: the z-streamed kernel, two CTAs per SM
-    // at radius 1 (96 KB of planes each), one at radius 2 (142 KB)
+    // at radius 1 (96 KB of planes each), one at radius 2 (149 KB)
     if (P.dim == 3 && P.np <= 27 && P.n[0] < (1ll << 30) && P.n[1] < (1ll << 30) && P.n[2] < (1ll << 30) &&
         (P.n[2] + A3_TX - 1) / A3_TX * ((P.n[1] + A3_TY - 1) / A3_TY) < (1ll << 30)) {
         a.z3 = true;

@@ -8,15 +8,16 @@
 // order the one-step adjoint kernels use, so its lam is bit-identical to
 // theirs.
 //
-// A CTA owns 64 x 32 output columns x rows and a contiguous range of planes
+// A CTA owns 128 x 16 output columns x rows and a contiguous range of planes
 // (the grid's tile-planes are split evenly over the resident CTAs, two per
 // SM at radius 1).  The planes of lam and u, each with an x halo of 4 columns
 // and a y halo of r rows, pass through a ring of 2r + 3 shared-memory slots
 // filled by 16-byte cp.async copies (indices wrapped on periodic axes,
 // outside values filled on Dirichlet ones; each thread's copies are resolved
 // once per job), two planes ahead of the plane being computed; every grid
-// element is read from HBM once per pass (plus the halos).  Each thread owns
-// 4 x-points of 2 rows.  Weight-gradient terms: FP32 per thread over two
+// element is read from HBM once per pass (plus the halos: a 4-column x halo
+// costs whole DRAM sectors, so tiles are wide).  Each thread owns 4 x-points
+// of 2 rows; a warp spans a tile row.  Weight-gradient terms: FP32 per thread over two
 // planes (16 products per weight), an FP32 warp tree, then FP64 per warp in
 // shared memory across all planes of the launch, and a fixed-order FP64 sum
 // over warps into the CTA's partial slot -- deterministic for a given grid.
@@ -26,7 +27,10 @@
 
 namespace sg {
 
-constexpr int A3_TX = 64, A3_RY = 2, A3_TY = 16 * A3_RY, A3_XH = 4, A3_XW = A3_TX + 2 * A3_XH, A3_THREADS = 256;
+constexpr int A3_THREADS = 256, A3_LX = 32;           // lanes along x: a whole warp spans a tile row
+constexpr int A3_TX = 4 * A3_LX, A3_RY = 2;             // tile columns; rows per thread
+constexpr int A3_TY = (A3_THREADS / A3_LX) * A3_RY;     // tile rows
+constexpr int A3_XH = 4, A3_XW = A3_TX + 2 * A3_XH;
 constexpr int A3_PF = 2;   // planes in flight ahead of the ones in use
 
 struct Adj3Params {
@@ -173,8 +177,8 @@ __global__ void __launch_bounds__(A3_THREADS, 2) adjoint3d_kernel(const __grid_c
     float *lam_ring = a3_smem, *u_ring = a3_smem + NSL * SLOT;
     __shared__ double gacc[A3_THREADS / 32][NP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int hw = warp * 2 + (lane >> 4);   // half-warp: tile rows A3_RY hw ..
-    const int xl = (lane & 15) * 4;
+    const int hw = (warp * 32 + lane) / A3_LX;   // row group: tile rows A3_RY hw ..
+    const int xl = (lane % A3_LX) * 4;
     for (int i = threadIdx.x; i < (A3_THREADS / 32) * NP; i += A3_THREADS) (&gacc[0][0])[i] = 0.0;
     float gw[NP];
 #pragma unroll
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(A3_THREADS, 2) adjoint3d_kernel(const __grid_c
                 // in registers (C[0..2], rotated one plane per step, so each
                 // plane's centre rows are read from shared memory once); the
                 // rows above and below come from the slot, x-neighbours by
-                // shuffles (the half-warp's edge lanes read the slot's halo
+                // shuffles (the row's edge lanes read the slot's halo
                 // columns).
                 const int rbase = (hw * A3_RY + R) * A3_XW + A3_XH + xl;   // own first row in a slot
                 if (t == 0) {
@@ -253,15 +257,15 @@ __global__ void __launch_bounds__(A3_THREADS, 2) adjoint3d_kernel(const __grid_c
                 float lL[A3_RY], lR[A3_RY], uL[A3_RY], uR[A3_RY];
 #pragma unroll
                 for (int b = 0; b < A3_RY; ++b) {
-                    lL[b] = __shfl_up_sync(0xffffffffu, lamC[1][b][3], 1, 16);
-                    lR[b] = __shfl_down_sync(0xffffffffu, lamC[1][b][0], 1, 16);
-                    uL[b] = __shfl_up_sync(0xffffffffu, uC[1][b][3], 1, 16);
-                    uR[b] = __shfl_down_sync(0xffffffffu, uC[1][b][0], 1, 16);
-                    if ((lane & 15) == 0) {
+                    lL[b] = __shfl_up_sync(0xffffffffu, lamC[1][b][3], 1, A3_LX);
+                    lR[b] = __shfl_down_sync(0xffffffffu, lamC[1][b][0], 1, A3_LX);
+                    uL[b] = __shfl_up_sync(0xffffffffu, uC[1][b][3], 1, A3_LX);
+                    uR[b] = __shfl_down_sync(0xffffffffu, uC[1][b][0], 1, A3_LX);
+                    if (lane % A3_LX == 0) {
                         lL[b] = lz[b * A3_XW - 1];
                         uL[b] = uz[b * A3_XW - 1];
                     }
-                    if ((lane & 15) == 15) {
+                    if (lane % A3_LX == A3_LX - 1) {
                         lR[b] = lz[b * A3_XW + 4];
                         uR[b] = uz[b * A3_XW + 4];
                     }
