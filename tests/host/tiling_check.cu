@@ -4,7 +4,12 @@
 // every row or plane in exactly one tile, the last one possibly shorter --
 // and tiles must keep the minimum lengths the kernels assume (max(4 r k, 16)
 // rows in 2D, max(4 r k, 8) planes in 3D, unless the axis itself is
-// shorter); an explicit tile length is honoured within those bounds.
+// shorter); an explicit tile length is honoured within those bounds.  The x
+// and y tiling of the 3D kernel (f3_axis, with the TMA path's narrower x halo
+// f3_hx): outputs partition the axis, every window holds its outputs plus the
+// r k halo (clipped at a Dirichlet domain's ends), Dirichlet windows stay in
+// the domain, and on the TMA path every window starts on a 16-byte boundary
+// (a TMA copy at an unaligned x raises an illegal-instruction fault).
 // Prints "ok <cases>" and exits 0, or the first failing case and exits 1.
 #include <cstdio>
 
@@ -57,6 +62,42 @@ int main() {
                         }
                         ++cases;
                     }
+    // 3D window tiling of one axis: W columns (window), AL elements per 16
+    // bytes, halo h = f3_hx (TMA) or the AL-rounded halo (periodic / cp.async)
+    const int geoms[][2] = {{32, 2}, {64, 4}, {64, 8}};   // FP64, FP32/int32, BF16/F16
+    for (const auto &gm : geoms)
+        for (int rk = 1; rk <= 4; ++rk)
+            for (int tma = 0; tma <= 1; ++tma)
+                for (int dir = 0; dir <= 1; ++dir) {
+                    if (tma && !dir) continue;   // periodic grids never use TMA
+                    const int W = gm[0], al = gm[1];
+                    const int h = tma ? sg::f3_hx(rk, W, al) : (rk + al - 1) / al * al;
+                    if (W - 2 * h < 1) continue;
+                    for (long long n = 1; n <= 700; ++n) {
+                        if (tma && n % al != 0) continue;   // TMA needs 16-byte rows
+                        const sg::F3Axis a = sg::f3_axis(n, W, h, dir != 0);
+                        long long next = 0;
+                        bool ok = h >= rk;
+                        for (int t = 0; t < a.T && ok; ++t) {
+                            int os, oe, ws;
+                            sg::f3_tile(a, t, os, oe, ws);
+                            ok = os == next && oe > os && oe <= n;
+                            next = oe;
+                            const long long need_lo = dir ? (os - rk > 0 ? os - rk : 0) : os - rk;
+                            const long long need_hi = dir ? (oe + rk < n ? oe + rk : n) : oe + rk;
+                            ok = ok && ws <= need_lo && ws + W >= need_hi;
+                            if (dir && n > W) ok = ok && ws >= 0 && ws + W <= n;
+                            if (tma) ok = ok && ws % al == 0;
+                        }
+                        ok = ok && next == n;
+                        if (!ok) {
+                            std::printf("FAIL 3D axis W=%d al=%d rk=%d tma=%d dir=%d n=%lld h=%d\n", W, al, rk, tma,
+                                        dir, n, h);
+                            return 1;
+                        }
+                        ++cases;
+                    }
+                }
     std::printf("ok %lld\n", cases);
     return 0;
 }

@@ -1,8 +1,8 @@
 """Host-side logic of the CUDA library that needs no GPU, compiled by nvcc as
 host code: the dependency sets of the persistent multi-pass kernels
 (tile_span in common.cuh) against brute force, and the tile geometry of the
-fused kernels (f2_tiling, f3_lz) against its covering and minimum-length
-rules."""
+fused kernels (f2_tiling, f3_lz, f3_axis with the TMA path's x halo f3_hx)
+against its covering, halo, minimum-length and 16-byte alignment rules."""
 
 import os
 import shutil
