@@ -734,7 +734,7 @@ def main():
     # through stencil_run_host (copy in, sweep, copy out back to back)
     h_in = u0.pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
-    NH = 4
+    NH = 8 if p.npts * esize <= 2**28 else 4   # enough grids to amortise the pipeline's fill and drain
     h_ins = [h_in] + [h_in.clone().pin_memory() for _ in range(NH - 1)]
     h_outs = [h_out] + [torch.empty_like(h_in).pin_memory() for _ in range(NH - 1)]
 
