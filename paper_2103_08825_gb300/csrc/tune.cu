@@ -170,7 +170,7 @@ extern "C" stencil_status_t stencil_plan_tune(stencil_plan_t P, int64_t T, void 
         for (int r : {32, 48, 64, 96, 128, 192})
             if (r < P->n[1]) rows_c.push_back(r);
     if (P->dim == 3)
-        for (int r : {16, 32, 48, 64, 96})
+        for (int r : {16, 32, 48, 64, 96, 128, 192})
             if (r < P->n[0]) rows_c.push_back(r);
     if (P->dim == 1)
         for (int r : {2, 4, 8, 16, 32})
