@@ -29,6 +29,8 @@
 // bit-identical to stencil_run's.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "k_fused2d.cuh"
 #include "plan.h"
@@ -65,6 +67,23 @@ __host__ __device__ __forceinline__ void tess_range(const TessAxis &a, bool inve
             if (lo < 0) lo = 0;
             if (hi > a.n) hi = a.n;
         }
+    }
+}
+
+// The levels t at which tile i of the kind updates coordinate c (virtual) of
+// the axis: [lo, hi] (empty when lo > hi; hi open-ended for an expanding tile).
+__host__ __device__ __forceinline__ void tess_levels(const TessAxis &a, bool inverted, int i, int c, int r, int &lo,
+                                                     int &hi) {
+    if (!inverted) {
+        // c in [e_i + t r, e_{i+1} - t r)  <=>  t r <= min(c - e_i, e_{i+1} - 1 - c)
+        const int m = min(c - tess_cut(a, i), tess_cut(a, i + 1) - 1 - c);
+        lo = 1;
+        hi = m < 0 ? 0 : m / r;
+    } else {
+        // c in [e - t r, e + t r)  <=>  t r >= e - c and t r > c - e
+        const int e = tess_cut(a, i);
+        lo = c >= e ? (c - e) / r + 1 : (e - c + r - 1) / r;
+        hi = 1 << 30;
     }
 }
 
@@ -188,6 +207,148 @@ __global__ void __launch_bounds__(256) tess_kernel(const __grid_constant__ TessP
     }
 }
 
+// The same stage with each tile's levels in shared memory: the tile loads
+// both level-parity buffers over its region -- per axis the union of its
+// ranges over the levels (the first level's range for a shrinking tile, the
+// last one's for an expanding tile) plus r on every side -- once, advances
+// levels 1..hlev there (each level read from the parity buffer of the level
+// before), and writes both buffers back at the points it updated.  Every value
+// a level reads is this tile's own earlier level or a value an earlier stage
+// left in the parity buffers (as in tess_kernel); within a stage every point
+// is updated by one tile only, and nothing else in the stage writes the
+// buffers there, so the result is tess_kernel's, bit for bit.  The launcher uses it
+// where the region fits in shared memory and does not wrap onto itself.
+template <int DT, int D, int R, int PAT>
+__global__ void __launch_bounds__(256) tess_smem_kernel(const __grid_constant__ TessParams<typename Traits<DT>::C> p) {
+    using S = typename Traits<DT>::S;
+    using C = typename Traits<DT>::C;
+    using Sh = Shape<D, R, PAT>;
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const TessGeo &g = p.geo;
+    const int n[3] = {g.ax[0].n, g.ax[1].n, g.ax[2].n};
+    const bool periodic = p.g.bkind == STENCIL_PERIODIC;
+    const C bval = p.g.bval;
+    S *const gb0 = static_cast<S *>(p.buf[0]);
+    S *const gb1 = static_cast<S *>(p.buf[1]);
+    for (int tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
+        int mask, idx[3];
+        tess_tile(g, tile, mask, idx);
+        int ulo[3], uhi[3], elo[3], ext[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a < 3 - D) {
+                ulo[a] = 0;
+                uhi[a] = 1;
+                elo[a] = 0;
+                ext[a] = 1;
+            } else {
+                const bool inv = (mask >> (a - (3 - D))) & 1;
+                tess_range(g.ax[a], inv, idx[a], inv ? p.hlev : 1, R, ulo[a], uhi[a]);
+                elo[a] = ulo[a] - R;
+                ext[a] = uhi[a] - ulo[a] + 2 * R;
+            }
+        }
+        const int ne = ext[0] * ext[1] * ext[2];
+        S *const s0 = reinterpret_cast<S *>(tsm);
+        S *const s1 = s0 + ne;
+        // physical index of virtual (z, y, x), or -1 outside a Dirichlet domain
+        auto phys = [&](int z, int y, int x) -> int64_t {
+            if (z < 0 || z >= n[0]) { if (!periodic) return -1; z = (int)wrap_idx(z, n[0]); }
+            if (y < 0 || y >= n[1]) { if (!periodic) return -1; y = (int)wrap_idx(y, n[1]); }
+            if (x < 0 || x >= n[2]) { if (!periodic) return -1; x = (int)wrap_idx(x, n[2]); }
+            return ((int64_t)z * n[1] + y) * n[2] + x;
+        };
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+            const int q1 = q / ext[2], q0 = q1 / ext[1];
+            const int64_t i = phys(elo[0] + q0, elo[1] + (q1 - q0 * ext[1]), elo[2] + (q - q1 * ext[2]));
+            s0[q] = i >= 0 ? gb0[i] : from_c<S>(bval);
+            s1[q] = i >= 0 ? gb1[i] : from_c<S>(bval);
+        }
+        __syncthreads();
+        for (int t = 1; t <= p.hlev; ++t) {
+            const S *src = ((p.t0 + t - 1) & 1) ? s1 : s0;
+            S *dst = ((p.t0 + t) & 1) ? s1 : s0;
+            int lo[3], hi[3];
+            int cnt = 1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a < 3 - D) {
+                    lo[a] = 0;
+                    hi[a] = 1;
+                } else {
+                    tess_range(g.ax[a], (mask >> (a - (3 - D))) & 1, idx[a], t, R, lo[a], hi[a]);
+                }
+                cnt *= hi[a] > lo[a] ? hi[a] - lo[a] : 0;
+            }
+            const int e1 = hi[1] - lo[1], e2 = hi[2] - lo[2];
+            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+                const int qq = q / e2;
+                const int q1 = qq / e1;
+                // shared-memory coordinates of the point
+                const int c0 = lo[0] + q1 - elo[0], c1 = lo[1] + (qq - q1 * e1) - elo[1],
+                          c2 = lo[2] + (q - qq * e2) - elo[2];
+                C acc = C(0);
+                bool first = true;
+#pragma unroll
+                for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz)
+#pragma unroll
+                    for (int oy = (D >= 2 ? -R : 0); oy <= (D >= 2 ? R : 0); ++oy)
+#pragma unroll
+                        for (int ox = -R; ox <= R; ++ox) {
+                            if (!Sh::inc(oz, oy, ox)) continue;
+                            const C v = to_c(src[((c0 + oz) * ext[1] + (c1 + oy)) * ext[2] + (c2 + ox)]);
+                            const C w = p.w[Sh::widx(oz, oy, ox)];
+                            acc = first ? op_mul(w, v) : op_fma(w, v, acc);
+                            first = false;
+                        }
+                dst[(c0 * ext[1] + c1) * ext[2] + c2] = from_c<S>(acc);
+            }
+            __syncthreads();
+        }
+        // both parity buffers back at the points this tile updated at some
+        // level (the product of its per-axis unions also holds points that
+        // another tile of the same stage, inverted on another axis, updates)
+        const int u1 = uhi[1] - ulo[1], u2 = uhi[2] - ulo[2];
+        const int nu = (uhi[0] - ulo[0]) * u1 * u2;
+        for (int q = threadIdx.x; q < nu; q += blockDim.x) {
+            const int qq = q / u2, q0 = qq / u1;
+            const int z = ulo[0] + q0, y = ulo[1] + (qq - q0 * u1), x = ulo[2] + (q - qq * u2);
+            const int c3[3] = {z, y, x};
+            int tlo = 1, thi = p.hlev;
+#pragma unroll
+            for (int a = 3 - D; a < 3; ++a) {
+                int lo, hi;
+                tess_levels(g.ax[a], (mask >> (a - (3 - D))) & 1, idx[a], c3[a], R, lo, hi);
+                tlo = max(tlo, lo);
+                thi = min(thi, hi);
+            }
+            if (tlo > thi) continue;   // not one of this tile's points at any level
+            const int64_t i = phys(z, y, x);
+            if (i < 0) continue;
+            const int c = ((z - elo[0]) * ext[1] + (y - elo[1])) * ext[2] + (x - elo[2]);
+            gb0[i] = s0[c];
+            gb1[i] = s1[c];
+        }
+        __syncthreads();   // the next tile reuses the shared memory
+    }
+}
+
+// Shared memory the smem kernel needs for geometry g (0: it does not apply --
+// a region larger than the budget, or wrapping onto itself on a periodic axis)
+inline size_t tess_smem_bytes(const TessGeo &g, int r, size_t elem) {
+    size_t pts = 1;
+    for (int a = 0; a < 3; ++a) {
+        const TessAxis &x = g.ax[a];
+        if (x.n == 1 && x.b == 1) continue;   // padded axis
+        const int seg = x.m <= 1 ? x.n : std::max(x.b, x.n - (x.m - 1) * x.b);
+        const int inv = 2 * g.h * r + 2 * r;
+        if (x.periodic && inv > x.n) return 0;
+        pts *= (size_t)std::max(seg, inv);
+    }
+    const size_t bytes = 2 * pts * elem;
+    return bytes <= 160 * 1024 ? bytes : 0;
+}
+
 template <int DT, int D, int R, int PAT>
 cudaError_t launch_tess_t(const stencil_plan_s &P, const TessGeo &geo, void *b0, void *b1, int t0, int hlev,
                           cudaStream_t st) {
@@ -205,8 +366,25 @@ cudaError_t launch_tess_t(const stencil_plan_s &P, const TessGeo &geo, void *b0,
     p.geo = geo;
     for (int j = 0; j < P.np; ++j) p.w[j] = conv_w<C>(P.w_eval[j]);
     int64_t grid = geo.tiles;
-    if (grid > (int64_t)P.sm_count * 8) grid = (int64_t)P.sm_count * 8;
     if (grid < 1) return cudaSuccess;
+    const size_t smem = tess_smem_bytes(geo, R, sizeof(typename Traits<DT>::S));
+    if (smem > 0) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(tess_smem_kernel<DT, D, R, PAT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        int bps = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tess_smem_kernel<DT, D, R, PAT>, 256,
+                                                                      smem);
+        if (e != cudaSuccess) return e;
+        grid = std::min<int64_t>(grid, (int64_t)P.sm_count * std::max(bps, 1));
+        tess_smem_kernel<DT, D, R, PAT><<<(unsigned)grid, 256, smem, st>>>(p);
+        return cudaGetLastError();
+    }
+    if (grid > (int64_t)P.sm_count * 8) grid = (int64_t)P.sm_count * 8;
     tess_kernel<DT, D, R, PAT><<<(unsigned)grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }

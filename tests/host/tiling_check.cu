@@ -9,12 +9,15 @@
 // f3_hx): outputs partition the axis, every window holds its outputs plus the
 // r k halo (clipped at a Dirichlet domain's ends), Dirichlet windows stay in
 // the domain, and on the TMA path every window starts on a 16-byte boundary
-// (a TMA copy at an unaligned x raises an illegal-instruction fault).
+// (a TMA copy at an unaligned x raises an illegal-instruction fault).  The
+// tessellation's closed-form level interval of a coordinate (tess_levels)
+// against membership in the per-level ranges (tess_range).
 // Prints "ok <cases>" and exits 0, or the first failing case and exits 1.
 #include <cstdio>
 
 #include "k_fused2d.cuh"
 #include "k_fused3d.cuh"
+#include "k_tess.cuh"
 
 static bool cover(long long n, long long len, long long tiles) {
     return len >= 1 && tiles >= 1 && tiles * len >= n && (tiles - 1) * len < n;
@@ -97,6 +100,33 @@ int main() {
                         }
                         ++cases;
                     }
+                }
+    // tess_levels: t in [lo, hi]  <=>  c in tess_range(t), for every in-domain c
+    for (int periodic = 0; periodic <= 1; ++periodic)
+        for (int n : {8, 9, 31, 64, 100})
+            for (int b : {4, 8, 16, 32})
+                for (int r = 1; r <= 3; ++r) {
+                    sg::TessAxis ax{n, b < n ? b : n, 0, periodic};
+                    ax.m = ax.n < 2 * ax.b ? 1 : ax.n / ax.b;
+                    for (int inv = 0; inv <= 1; ++inv)
+                        for (int i = 0; i < sg::tess_count(ax, inv != 0); ++i)
+                            for (int c = -3 * b; c < n + 3 * b; ++c) {
+                                int lo, hi;
+                                sg::tess_levels(ax, inv != 0, i, c, r, lo, hi);
+                                for (int t = 1; t <= 12; ++t) {
+                                    int rl, rh;
+                                    sg::tess_range(ax, inv != 0, i, t, r, rl, rh);
+                                    const bool in_range = c >= rl && c < rh;
+                                    const bool in_dom = periodic || (c >= 0 && c < n);
+                                    if (!in_dom) continue;
+                                    if (in_range != (t >= lo && t <= hi)) {
+                                        std::printf("FAIL tess_levels n=%d b=%d r=%d periodic=%d inv=%d i=%d c=%d t=%d\n",
+                                                    n, b, r, periodic, inv, i, c, t);
+                                        return 1;
+                                    }
+                                    ++cases;
+                                }
+                            }
                 }
     std::printf("ok %lld\n", cases);
     return 0;
