@@ -82,8 +82,9 @@ typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_ki
  * launch per stage; segments of the plan's tile length (default 2048, 64, 32
  * points in 1D, 2D, 3D; a tile must stay below 2^31 points).  Results are
  * bit-identical to the other forms.  On GB300 it runs well below the fused
- * forms (its levels go through L2 and each stage is a launch): it is there
- * as the paper's scheme, not as a fast path. */
+ * forms (each stage is a launch, each level a CTA barrier, and a tile loads and
+ * writes back both level buffers): it is there as the paper's scheme, not as a
+ * fast path. */
 typedef enum {
     STENCIL_VARIANT_FUSED = 0,
     STENCIL_VARIANT_PLAIN = 1,
