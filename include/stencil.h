@@ -79,8 +79,8 @@ typedef enum { STENCIL_DIRICHLET = 0, STENCIL_PERIODIC = 1 } stencil_boundary_ki
  * levels (h = the plan's k, default 8; any h with 2 h r no longer than a
  * segment), each in d + 1 stages of concurrent shrinking / expanding tiles
  * that together update every point once per level -- no redundant work, one
- * launch per stage; segments of the plan's tile length (default 2048, 64, 32
- * points in 1D, 2D, 3D; a tile must stay below 2^31 points).  Results are
+ * launch per stage; segments of the plan's tile length (default 2048, 64, 16
+ * points in 1D, 2D, 3D, at least 2 h r; a tile must stay below 2^31 points).  Results are
  * bit-identical to the other forms.  On GB300 it runs well below the fused
  * forms (each stage is a launch, each level a CTA barrier, and a tile loads and
  * writes back both level buffers): it is there as the paper's scheme, not as a

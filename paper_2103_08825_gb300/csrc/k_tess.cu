@@ -10,7 +10,9 @@
 namespace sg {
 
 // default segment length by dimension (at least 2 h r)
-static int tess_default_b(int d) { return d == 1 ? 2048 : d == 2 ? 64 : 32; }
+// default segment length: 2048, 64, 16 points in 1D, 2D, 3D -- the 3D tile's
+// two level buffers then fit in shared memory (16^3 points)
+static int tess_default_b(int d) { return d == 1 ? 2048 : d == 2 ? 64 : 16; }
 
 // Axes for extents n (outermost first, d of them), tile length b, h levels,
 // radius r; false if some segment is shorter than 2 h r.
