@@ -327,10 +327,25 @@ def stencil_adjoint_vc(plan: Plan, coef, u0, grad_uT, T: int, ckpt_every: int, g
                                      _stream_handle(stream)), "stencil_adjoint_vc")
     return grad_u0, grad_coef
 
+def _host_grid(plan: Plan, a, name: str) -> int:
+    """Address of a host grid (numpy array or CPU tensor) after checking that
+    it is contiguous, on the host and exactly one grid of the plan's dtype."""
+    import numpy as np
+    npts = int(np.prod(plan.shape))
+    size = {STENCIL_F64: 8, STENCIL_F32: 4, STENCIL_BF16: 2, STENCIL_F16: 2, STENCIL_I32: 4}[plan.dtype]
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous() or _dtype_code(a.dtype) != plan.dtype or a.numel() != npts:
+            raise ValueError(f"{name} must be a contiguous CPU tensor of {npts} values of the plan's dtype")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.size != npts or a.itemsize != size:
+        raise ValueError(f"{name} must be a contiguous array of {npts} values of the plan's dtype")
+    return a.ctypes.data
+
+
 def stencil_run_host(plan: Plan, h_in, h_out, T: int, stream=None):
     """Host-buffer run (numpy arrays or CPU tensors); synchronises."""
     def ptr(a):
-        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        return _host_grid(plan, a, "host grid")
     _check(load().stencil_run_host(plan.handle, ctypes.c_void_p(ptr(h_in)), ctypes.c_void_p(ptr(h_out)), int(T),
                                    _stream_handle(stream)), "stencil_run_host")
     return h_out
@@ -340,7 +355,7 @@ def stencil_run_host_many(plan: Plan, h_ins, h_outs, T: int, stream=None):
     """h_outs[i] := T steps of h_ins[i] (host arrays or CPU tensors; pinned
     memory makes the copies overlap the sweeps); synchronises."""
     def ptr(a):
-        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        return _host_grid(plan, a, "host grid")
     n = len(h_ins)
     if len(h_outs) != n:
         raise ValueError("one output per input")
